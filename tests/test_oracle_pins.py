@@ -1,0 +1,377 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test names what it pins and the paper passage (or the mathematics) that fixes the expected
+value.  A plausible mistake anywhere in the oracle (a dropped term, a wrong sign, a wrong unit, a
+transposed operand, a wrong tableau entry) makes at least one of them fail.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+from scipy.linalg import expm
+
+from bulb_inputs import Workload, number_luminosity_bins
+from oracle import physics as ph
+from oracle import four_psi
+from oracle.expm import two_flavor_propagator, hermitian_propagator
+from oracle.integrate import (evolve_fixed, evolve_adaptive, cf4_step, rk4_step, dp45_step,
+                              DP_A, DP_B, DP_BHAT, DP_C)
+from oracle.physics import Bulb, Grid, cos_theta
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
+NO_L = {k: 0.0 for k in ("nue", "nuebar", "nux", "nuxbar")}
+
+
+def golden(name):
+    for line in open(GOLDEN):
+        if line.startswith(name):
+            return line.split()[1]
+    raise KeyError(name)
+
+
+def pee(Y):
+    return Y[..., 0, 0].real
+
+
+def bloch(M):
+    """Bloch vector of the traceless part of 2x2 Hermitian matrices: M = (1/2) j . sigma + tr."""
+    return np.stack([2 * M[..., 0, 1].real, -2 * M[..., 0, 1].imag,
+                     (M[..., 0, 0] - M[..., 1, 1]).real], axis=-1)
+
+
+# --- units and constants ------------------------------------------------------------------------
+def test_fermi_constant_matches_paper():
+    """Sec. 2 prints G_F ~ 1.166e-5 GeV^-2."""
+    assert abs(ph.G_F_GEV2 - float(golden("G_F_GeV-2"))) < 0.0005e-5
+
+
+def test_matter_potential_textbook_value():
+    """sqrt(2) G_F n_e = 7.63e-14 eV per (Ye rho / g cm^-3): pins G_F, hbar c, m_u and km units."""
+    wl = Workload(name="m", matter="constant")
+    n_e = 1.0 / ph.M_U_G * ph.CM3_PER_KM3            # Ye rho = 1 g/cm^3, per km^3
+    lam_kmi = ph.sqrt2_GF_kmi_per_km3() * n_e
+    lam_eV = lam_kmi * ph.HBARC_EV_KM
+    assert abs(lam_eV / float(golden("V_CC_eV_per_Ye_rho")) - 1) < 2e-3
+
+
+def test_initial_condition_matches_paper():
+    """Sec. 3.4: electron-flavour neutrinos and antineutrinos start as (1, 0)."""
+    wl = Workload(name="ic", n_energy=3, n_angle=2)
+    Y = Bulb(wl).initial_state()
+    e = np.array([float(x) for x in golden("psi_nue_initial").split(",")])
+    assert np.array_equal(Y[..., :, :].real, np.broadcast_to(np.outer(e, e), Y.shape))
+
+
+# --- Eq. U -----------------------------------------------------------------------------------------
+def test_eq_u_equals_matrix_exponential():
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((50, 2, 2)) + 1j * rng.standard_normal((50, 2, 2))
+    H = A + np.conj(np.swapaxes(A, -1, -2))
+    dl = rng.uniform(0.0, 5.0, 50)
+    U = two_flavor_propagator(H, dl)
+    for i in range(50):
+        assert np.abs(U[i] - expm(-1j * dl[i] * H[i])).max() < 1e-13
+    # lambda = 0 (H proportional to the identity) is the degenerate case of Eq. U
+    Hd = np.broadcast_to(np.eye(2) * 3.0, (1, 2, 2)).astype(complex)
+    assert np.abs(two_flavor_propagator(Hd, 0.5)[0] - np.exp(-1.5j) * np.eye(2)).max() < 1e-15
+
+
+def test_hermitian_exponential_equals_matrix_exponential():
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((30, 3, 3)) + 1j * rng.standard_normal((30, 3, 3))
+    H = A + np.conj(np.swapaxes(A, -1, -2))
+    U = hermitian_propagator(H, 0.3)
+    for i in range(30):
+        assert np.abs(U[i] - expm(-0.3j * H[i])).max() < 1e-13
+
+
+# --- closed forms -----------------------------------------------------------------------------------
+def _vacuum_pee(wl, grid, r, dm2, theta):
+    """P_ee = 1 - sin^2 2theta sin^2(1.267 dm2 L/E) with the path length L of each beam (km),
+    E in GeV; L = r cos theta(r) - R cos theta_R for straight-line propagation from R."""
+    c = cos_theta(grid.u, wl.R_km, r)
+    L = r * c - wl.R_km * np.sqrt(1.0 - grid.u)
+    phase = float(golden("osc_phase_coeff")) * dm2 * L[:, None] / (grid.E[None, :] * 1e-3)
+    return 1.0 - math.sin(2 * theta) ** 2 * np.sin(phase) ** 2
+
+
+@pytest.mark.parametrize("method", ["rk4", "lie_rk4", "dp45"])
+def test_vacuum_closed_form(method):
+    """mu = lambda = 0: every beam oscillates as in vacuum along its own path length."""
+    wl = Workload(name="vac", n_energy=7, n_angle=5, L=NO_L, dm2=(2.4e-3, 0.0), theta=(0.3, 0, 0))
+    b = Bulb(wl)
+    Y0 = b.initial_state()
+    if method == "dp45":
+        Y, r, _ = evolve_adaptive(b, Y0, 11.0, 31.0, 1e-11, 1e-11, 1e-3)
+    else:
+        Y, _ = evolve_fixed(b, Y0, 11.0, 31.0, 4000, method)
+    ref = _vacuum_pee(wl, b.grid, 31.0, 2.4e-3, 0.3)
+    # the textbook 1.267 has four digits: the phase (up to ~30 rad) carries ~1e-4 relative error
+    assert np.abs(pee(Y[0]) - ref).max() < 5e-3
+    assert np.abs(pee(Y[1]) - ref).max() < 5e-3
+    # with the exact coefficient 1/(4 hbar c) the agreement is at the integrator's accuracy
+    exact = 1.0 / (4 * ph.HBARC_EV_KM * 1e6)       # dm2 L / (4 E) with E in MeV, L in km
+    c = cos_theta(b.grid.u, wl.R_km, 31.0)
+    L = 31.0 * c - wl.R_km * np.sqrt(1.0 - b.grid.u)
+    ref2 = 1 - math.sin(0.6) ** 2 * np.sin(exact * 2.4e-3 * L[:, None] / b.grid.E[None, :]) ** 2
+    assert np.abs(pee(Y[0]) - ref2).max() < 2e-9
+    assert abs(exact / 1e3 / float(golden("osc_phase_coeff")) - 1) < 1e-3
+
+
+@pytest.mark.parametrize("sign", [+1.0, -1.0])
+def test_constant_matter_closed_form(sign):
+    """Constant lambda, mu = 0: MSW in uniform matter.  Neutrinos see +lambda, antineutrinos
+    -lambda (Eq. eom), with Delta_m = sqrt((omega cos 2th - lambda)^2 + omega^2 sin^2 2th)."""
+    dm2 = sign * 2.4e-3
+    wl = Workload(name="msw", n_energy=6, n_angle=4, L=NO_L, dm2=(dm2, 0.0), theta=(0.15, 0, 0),
+                  matter="constant", lambda_const=0.4)
+    b = Bulb(wl)
+    Y, _ = evolve_fixed(b, b.initial_state(), 11.0, 21.0, 1000, "lie_rk4")
+    c = cos_theta(b.grid.u, wl.R_km, 21.0)
+    L = 21.0 * c - wl.R_km * np.sqrt(1.0 - b.grid.u)
+    omega = dm2 / (2 * b.grid.E * 1e6 * ph.HBARC_EV_KM)
+    for species, lam in ((0, 0.4), (1, -0.4)):
+        D = np.sqrt((omega * math.cos(0.3) - lam) ** 2 + (omega * math.sin(0.3)) ** 2)
+        s2m = (omega * math.sin(0.3)) ** 2 / D**2
+        ref = 1 - s2m[None, :] * np.sin(0.5 * D[None, :] * L[:, None]) ** 2
+        assert np.abs(pee(Y[species]) - ref).max() < 1e-10
+
+
+# --- equation structure -----------------------------------------------------------------------------
+def test_antineutrino_conjugated_convention():
+    """Evolving Pbar with Hbar = H_vac - H_mat - H_nunu^* is the same as evolving sigma = Pbar^*
+    with -H_vac + H_mat + H_nunu (complex conjugate of Eq. eom, real H_vac and H_mat)."""
+    wl = Workload(name="c", n_energy=4, n_angle=3, matter="constant", lambda_const=2.0)
+    b = Bulb(wl)
+    rng = np.random.default_rng(3)
+    from bulb_inputs import random_unit_states
+    psi = random_unit_states(2, 2 * 3 * 4, seed=11).reshape(2, 3, 4, 2)
+    Y = psi[..., :, None] * np.conj(psi[..., None, :])
+    r = 40.0
+    dY = b.rhs(r, Y)
+    Hnn = b.nunu_hamiltonian(r, Y[0], Y[1])[:, None]
+    Hs = -b.Hvac[None] + 2.0 * b.Pe + Hnn
+    sigma = np.conj(Y[1])
+    dsigma = -1j * (Hs @ sigma - sigma @ Hs) / b.cos_theta(r)[:, None, None, None]
+    assert np.abs(np.conj(dY[1]) - dsigma).max() < 1e-12 * np.abs(dsigma).max()
+
+
+def test_single_angle_geometric_factor():
+    """With every beam in the same state, H_nunu of a radial beam (cos th = 1) is proportional to
+    int_0^1 du (1/sqrt(1 - u x) - 1) = (1 - sqrt(1 - x))^2 / x, x = R^2/r^2 (Eq. Hnu integrated
+    in closed form); the midpoint u-bins converge to it at second order."""
+    r = 22.0
+    x = (11.0 / r) ** 2
+    D_exact = (1 - math.sqrt(1 - x)) ** 2 / x
+    errs = []
+    for Nu in (16, 32, 64):
+        wl = Workload(name="sa", n_energy=3, n_angle=Nu)
+        u = np.concatenate([(np.arange(Nu) + 0.5) / Nu, [0.0]])       # add a radial probe bin
+        du = np.concatenate([np.full(Nu, 1.0 / Nu), [0.0]])
+        b = Bulb(wl, grid=Grid.from_workload(wl, u=u, du=du))
+        Y = b.initial_state()
+        Y[..., 0, 1] = 0.3
+        Y[..., 1, 0] = 0.3                  # same (non-diagonal) state in every beam
+        H = b.nunu_hamiltonian(r, Y[0], Y[1])[-1]           # the radial probe bin
+        F = b.flux_matrices(Y[0], Y[1])[0].sum(axis=0)      # energy-integrated flux of one bin
+        mu = b.K * 11.0**2 / (2 * r * r)                   # K R^2/(2 r^2)
+        D_num = (H[0, 1] / (mu * F[0, 1])).real
+        errs.append(abs(D_num - D_exact))
+    assert errs[-1] < 2e-3 * D_exact
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
+def test_lepton_number_invariant():
+    """With lambda = 0 the continuous bulb equations conserve Tr(M J1), M the unit vacuum matrix:
+    sum_b g_b B.(h_b x s_b)/c_b = mu B.(j0 x j0 - j1 x j1) = 0.  Matter breaks it."""
+    wl = Workload(name="ln", n_energy=6, n_angle=5)
+    b = Bulb(wl)
+    M = np.array([[-math.cos(0.2), math.sin(0.2)], [math.sin(0.2), math.cos(0.2)]])
+    drift = {}
+    for matter in ("none", "constant"):
+        wl.matter, wl.lambda_const = matter, 30.0
+        b = Bulb(wl)
+        vals = []
+        def cb(n, r, Y):
+            J0, J1 = b.moment_matrices(r, Y)
+            vals.append(np.trace(M @ J1).real)
+        Y0 = b.initial_state()
+        evolve_fixed(b, Y0, 70.0, 80.0, 400, "rk4", callback=cb)
+        scale = np.abs(b.moment_matrices(70.0, Y0)[1]).max()
+        drift[matter] = (max(vals) - min(vals)) / scale
+    assert drift["none"] < 1e-9
+    assert drift["constant"] > 1e-4
+
+
+def _sync_rate(mu0, n_energy=4, span=3.0, chunks=30):
+    wl = Workload(name="sync", n_energy=n_energy, n_angle=1, E_min=5.0, E_max=30.0,
+                  dm2=(2.4e-3, 0.0), theta=(0.2, 0, 0))
+    b = Bulb(wl, geometry="homogeneous", mu0=mu0)
+    N = b.grid.N
+    g_nu = N[0, 0] - N[0, 1]
+    g_bar = -(N[1, 0] - N[1, 1])
+    omega = 2.4e-3 / (2 * b.grid.E * 1e6 * ph.HBARC_EV_KM)
+    w_sync = (np.sum(omega * g_nu) - np.sum(omega * g_bar)) / (np.sum(g_nu) + np.sum(g_bar))
+    B = np.array([math.sin(0.4), 0.0, -math.cos(0.4)])
+    e1 = np.array([0.0, 0.0, 1.0]) + B * math.cos(0.4)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(B, e1)
+    Y, r, phases, rs = b.initial_state(), 0.0, [], []
+    for _ in range(chunks):
+        Y, r, _ = evolve_adaptive(b, Y, r, r + span / chunks, 1e-10, 1e-10, 1e-4)
+        j = bloch(b.moment_matrices(r, Y)[1])
+        phases.append(math.atan2(j @ e2, j @ e1))
+        rs.append(r)
+    return np.polyfit(rs, np.unwrap(phases), 1)[0], w_sync
+
+
+def test_synchronised_precession():
+    """Homogeneous geometry, mu0 >> omega: the collective vector J = sum_b g_b s_b precesses about
+    B at omega_sync = sum_b eta_b omega_b g_b / sum_b g_b (synchronised oscillation), with a
+    deviation that falls like 1/mu0."""
+    dev = []
+    for mu0 in (100.0, 1000.0):
+        slope, w_sync = _sync_rate(mu0)
+        dev.append(abs(slope / w_sync - 1))
+    # |J| is ~12% of the total flux here, so the effective coupling is ~0.12 mu0
+    assert dev[1] < 1.5e-2
+    assert dev[0] / dev[1] > 5.0
+
+
+def test_duplicated_angles_equal_single_angle():
+    """A multi-angle run whose bins all sit at the same u (weights summing to 1) equals the one-bin
+    run at that u, bin by bin."""
+    u_star = 0.37
+    wl1 = Workload(name="d1", n_energy=5, n_angle=1)
+    b1 = Bulb(wl1, grid=Grid.from_workload(wl1, u=[u_star], du=[1.0]))
+    wl4 = Workload(name="d4", n_energy=5, n_angle=4)
+    b4 = Bulb(wl4, grid=Grid.from_workload(wl4, u=[u_star] * 4, du=[0.25] * 4))
+    Y1, _ = evolve_fixed(b1, b1.initial_state(), 60.0, 70.0, 200, "rk4")
+    Y4, _ = evolve_fixed(b4, b4.initial_state(), 60.0, 70.0, 200, "rk4")
+    assert np.abs(pee(Y1)).min() < 0.999          # non-trivial evolution
+    for j in range(4):
+        assert np.abs(Y4[:, j] - Y1[:, 0]).max() < 1e-12
+
+
+# --- invariants ---------------------------------------------------------------------------------------
+def test_exponential_scheme_keeps_pure_states():
+    """exp(-i H dl) is unitary: Tr P = 1, P^2 = P and P = P^dag hold to rounding (Sec. 3.4, Eq. U)."""
+    wl = Workload(name="inv", n_energy=6, n_angle=5, matter="power_law")
+    b = Bulb(wl)
+    Y, _ = evolve_fixed(b, b.initial_state(), 40.0, 60.0, 100, "lie_rk4")
+    tr = np.trace(Y, axis1=-2, axis2=-1)
+    assert np.abs(tr - 1).max() < 1e-11
+    assert np.abs(Y @ Y - Y).max() < 1e-11
+    assert np.abs(Y - np.conj(np.swapaxes(Y, -1, -2))).max() < 1e-14
+
+
+def test_runge_kutta_trace_exact_purity_to_order():
+    wl = Workload(name="inv2", n_energy=6, n_angle=5)
+    b = Bulb(wl)
+    Y, _ = evolve_fixed(b, b.initial_state(), 70.0, 80.0, 400, "rk4")
+    assert np.abs(np.trace(Y, axis1=-2, axis2=-1) - 1).max() < 1e-13   # commutator: trace exact
+    purity = np.abs(Y @ Y - Y).max()                                      # purity only to O(h^4)
+    assert 1e-12 < purity < 1e-4
+
+
+# --- integrators --------------------------------------------------------------------------------------
+def _nonlinear_case():
+    wl = Workload(name="nl", n_energy=6, n_angle=5, r0=80, r1=82)
+    b = Bulb(wl)
+    return b, b.initial_state()
+
+
+def test_runge_kutta_agrees_with_library_integrator():
+    """The oracle's RK4 on its right-hand side matches scipy's DOP853 on the same right-hand side."""
+    b, Y0 = _nonlinear_case()
+    shape = Y0.shape
+    def f(r, y):
+        return b.rhs(r, y.reshape(shape)).ravel()
+    sol = solve_ivp(f, (80.0, 82.0), Y0.ravel(), method="DOP853", rtol=1e-13, atol=1e-13)
+    Yref = sol.y[:, -1].reshape(shape)
+    Y, _ = evolve_fixed(b, Y0, 80.0, 82.0, 2000, "rk4")
+    assert np.abs(Y - Yref).max() < 1e-10
+
+
+@pytest.mark.parametrize("method,order", [("rk4", 4), ("lie_rk4", 4), ("dp5", 5)])
+def test_convergence_order(method, order):
+    """Richardson: halving h divides the error by 2^order (classical RK4, CF4, Dormand-Prince 5)."""
+    b, Y0 = _nonlinear_case()
+    Yref, _ = evolve_fixed(b, Y0, 80.0, 82.0, 8000, "rk4")
+    errs = []
+    for n in (100, 200, 400):
+        if method == "dp5":
+            Y, h = Y0.copy(), 2.0 / n
+            k1 = b.rhs(80.0, Y)
+            for i in range(n):
+                Y, _, k1 = dp45_step(b.rhs, 80.0 + i * h, Y, h, k1, 1.0, 1.0)
+        else:
+            Y, _ = evolve_fixed(b, Y0, 80.0, 82.0, n, method)
+        errs.append(np.abs(Y - Yref).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(q - order) < 0.35 for q in rates), (errs, rates)
+
+
+def test_dormand_prince_tableau_consistency():
+    """Row sums of A equal c; both weight rows sum to 1 (consistency of the Butcher tableau)."""
+    for i in range(1, 7):
+        assert abs(sum(DP_A[i]) - DP_C[i]) < 1e-15
+    assert abs(DP_B.sum() - 1) < 1e-15 and abs(DP_BHAT.sum() - 1) < 1e-15
+
+
+def test_adaptive_controller_meets_tolerance():
+    b, Y0 = _nonlinear_case()
+    Yref, _ = evolve_fixed(b, Y0, 80.0, 82.0, 8000, "rk4")
+    Y, r, st = evolve_adaptive(b, Y0, 80.0, 82.0, 1e-8, 1e-8, 1e-3)
+    assert r == 82.0 and st.accepted > 5
+    assert np.abs(Y - Yref).max() < 1e-6
+
+
+# --- paper-literal state and flavour reductions -----------------------------------------------------
+@pytest.mark.parametrize("nf", [2, 3])
+def test_four_wavefunctions_equal_reduced_state(nf):
+    """Evolving every initial particle identity's wavefunction (Sec. 3.2 NBeam array, Sec. 2 flux
+    sum over alpha) equals evolving the electron-flavour density matrices with I - P for the rest."""
+    if nf == 2:
+        wl = Workload(name="4p", n_energy=5, n_angle=4, matter="constant", lambda_const=3.0)
+    else:
+        wl = Workload(name="4p3", n_flavor=3, n_energy=5, n_angle=4, dm2=(7.5e-5, -2.4e-3),
+                      theta=(0.59, 0.15, 0.785), matter="constant", lambda_const=3.0)
+    b = Bulb(wl)
+    Y, psi = b.initial_state(), four_psi.initial_wavefunctions(b)
+    r = 70.0
+    for _ in range(30):
+        Y = cf4_step(b.generators, r, Y, 0.1)
+        psi = four_psi.cf4_step(b, r, psi, 0.1)
+        r += 0.1
+    assert pee(Y).min() < 0.999
+    assert np.abs(four_psi.electron_density_matrices(psi) - Y).max() < 1e-12
+
+
+def test_three_flavours_reduce_to_two():
+    """theta12 = theta23 = 0, dm2_21 = 0: the e-tau sector is the two-flavour problem with
+    (dm2_31, theta13); the mu flavour decouples."""
+    wl2 = Workload(name="r2", n_energy=5, n_angle=4, dm2=(-2.4e-3, 0.0), theta=(0.1, 0, 0),
+                   matter="constant", lambda_const=1.0)
+    wl3 = Workload(name="r3", n_flavor=3, n_energy=5, n_angle=4, dm2=(0.0, -2.4e-3),
+                   theta=(0.0, 0.1, 0.0), matter="constant", lambda_const=1.0)
+    b2, b3 = Bulb(wl2), Bulb(wl3)
+    Y2, _ = evolve_fixed(b2, b2.initial_state(), 70.0, 75.0, 100, "rk4")
+    Y3, _ = evolve_fixed(b3, b3.initial_state(), 70.0, 75.0, 100, "rk4")
+    assert pee(Y2).min() < 0.999
+    assert np.abs(Y3[..., 0, 0] - Y2[..., 0, 0]).max() < 1e-12
+    assert np.abs(Y3[..., 0, 2] - Y2[..., 0, 1]).max() < 1e-12
+    assert np.abs(Y3[..., 1, 1]).max() < 1e-15
+
+
+def test_spectra_normalisation():
+    """Per-bin number luminosities sum to L/<E> per flavour (Sec. 2: L/<E> f(E), f normalised)."""
+    N = number_luminosity_bins(2, 64, 1.0, 60.0, {"nue": 1e51, "nuebar": 2e51, "nux": 3e51,
+                                                   "nuxbar": 3e51},
+                               {"nue": 11.0, "nuebar": 16.0, "nux": 25.0, "nuxbar": 25.0})
+    MeV = 1.602176634e-6
+    assert abs(N[0, 0].sum() / (1e51 / (11 * MeV)) - 1) < 1e-13
+    assert abs(N[1, 0].sum() / (2e51 / (16 * MeV)) - 1) < 1e-13
+    assert abs(N[1, 1].sum() / (3e51 / (25 * MeV)) - 1) < 1e-13
