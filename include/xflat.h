@@ -1,0 +1,243 @@
+/*
+ * xflat.h -- C ABI of the GB300 bulb-model radial-step solver.
+ *
+ * The solver advances the flavour density matrices of every neutrino and antineutrino beam of the
+ * stationary, spherically symmetric neutrino bulb model (arXiv:1912.10596, Sec. 2):
+ *
+ *   i cos(theta) d/dr psi     = [H_vac(E) + H_mat(r) + H_nunu(v;r)]   psi        (Eq. eom)
+ *   i cos(theta) d/dr psibar  = [H_vac(E) - H_mat(r) - H_nunu^*(v;r)] psibar
+ *
+ * with H_nunu the angular integral of the flux matrices of all beams (Eq. Hnu, Eq. F), from the
+ * initial conditions of Sec. 3.4 (electron flavour (1,0[,0]) at r = R).  A beam is one energy bin
+ * (equal-width bins in E) times one emission-angle bin (equal-width bins in u = sin^2 theta_R,
+ * Sec. 3.2) times one species (nu, nubar); beams are indexed
+ *
+ *   b = ((species * n_angle) + j) * n_energy + k,   species 0 = nu, 1 = nubar,
+ *
+ * energy fastest.  Units: r and R in km, E in MeV, Hamiltonians in 1/km, number luminosities in
+ * 1/s.  Every value crossing this boundary is IEEE double, whatever the internal precision.
+ *
+ * Conventions shared by all entry points
+ *  - Every function returns an int status (XFLAT_OK = 0); no C++ exception or abort crosses the ABI.
+ *    xflat_last_error() gives a one-line description of the last failure on a handle.
+ *  - A handle owns all device memory it allocates; host arrays are caller-owned and copied in or
+ *    out during the call; device pointers passed in are borrowed for the duration of the call.
+ *  - All device work is enqueued on the CUDA stream given in xflat_config.cuda_stream (NULL = the
+ *    legacy default stream); calls that return host data synchronise that stream.
+ *  - A handle is not thread-safe: one host thread at a time.
+ *  - Requires a GPU of compute capability 10.3 (sm_103a); on anything else xflat_create fails with
+ *    XFLAT_ERR_CUDA.  There is no CPU fallback.
+ */
+#ifndef XFLAT_H
+#define XFLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XFLAT_ABI_VERSION 1u
+
+/* ---- status codes ---------------------------------------------------------------------------- */
+enum xflat_status {
+  XFLAT_OK = 0,
+  XFLAT_ERR_INVAL = 1,        /* bad argument (size, range, NULL, layout)                       */
+  XFLAT_ERR_NOMEM = 2,        /* a device or host allocation failed                             */
+  XFLAT_ERR_CUDA = 3,         /* a CUDA runtime call failed (message in xflat_last_error)       */
+  XFLAT_ERR_TIMEOUT = 4,      /* a device-wide barrier exceeded barrier_timeout_ns              */
+  XFLAT_ERR_NONFINITE = 5,    /* a NaN or infinity appeared in the state, moments or error norm */
+  XFLAT_ERR_STEP = 6,         /* adaptive step size fell below h_min_km                         */
+  XFLAT_ERR_STATE = 7,        /* call order violated (e.g. evolve before set_spectra)           */
+  XFLAT_ERR_UNSUPPORTED = 8   /* valid request this build does not implement                    */
+};
+
+/* ---- configuration enums --------------------------------------------------------------------- */
+enum xflat_precision {
+  XFLAT_FP64 = 0,             /* every per-beam operation in IEEE double                         */
+  XFLAT_MIXED = 1             /* per-beam precession in float; moment reduction across threads,
+                                 warps, blocks and the grid, the error-norm maximum and the
+                                 step-size controller in double; |s| renormalised every step    */
+};
+enum xflat_integrator {
+  XFLAT_RK4 = 0,              /* classical 4-stage RK on d(rho)/dr = -i[H,rho]/cos(theta), fixed step */
+  XFLAT_DP45 = 1,             /* Dormand-Prince 5(4), FSAL, adaptive (error control below)        */
+  XFLAT_LIE_RK4 = 2           /* commutator-free Lie RK4 whose every update is an exact propagator
+                                 exp(-i H dl) of Eq. U (two flavours only), fixed step              */
+};
+enum xflat_matter {
+  XFLAT_MATTER_NONE = 0,
+  XFLAT_MATTER_POWER_LAW = 1, /* n_e = Ye rho0 (r_ref/r)^power / m_u                               */
+  XFLAT_MATTER_CONSTANT = 2   /* sqrt(2) G_F n_e = lambda_const_kmi at every r                     */
+};
+enum xflat_layout {
+  XFLAT_LAYOUT_MATRIX = 0,    /* [n_beams][n][n] complex double, interleaved (re, im), row major,
+                                 the paper's psi psi^dagger (antineutrinos: psibar psibar^dagger) */
+  XFLAT_LAYOUT_NATIVE = 1     /* [n_comp][n_beams] double planes of the internal state:
+                                 2 flavours n_comp = 3, Bloch vector s of the nu density matrix
+                                 P = (1 + s.sigma)/2 and of conj(Pbar) for antineutrinos;
+                                 3 flavours n_comp = 9: P00, P11, P22, Re P01, Im P01, Re P02,
+                                 Im P02, Re P12, Im P12 of P (nu) and of conj(Pbar) (nubar)     */
+};
+
+/* ---- configuration --------------------------------------------------------------------------- */
+typedef struct {
+  uint32_t abi_version;       /* must be XFLAT_ABI_VERSION                                         */
+  uint32_t n_flavor;          /* 2 or 3                                                            */
+  uint32_t n_energy;          /* energy bins, >= 1                                                 */
+  uint32_t n_angle;           /* emission-angle (u) bins, >= 1                                     */
+  uint32_t precision;         /* xflat_precision                                                   */
+  uint32_t integrator;        /* xflat_integrator                                                  */
+  uint32_t matter_kind;       /* xflat_matter                                                      */
+  uint32_t reserved0;
+  double R_km;                /* neutrino-sphere radius R                                          */
+  double E_min_MeV, E_max_MeV;/* energy range, bins of equal width, midpoints                      */
+  double dm2_eV2[2];          /* 2 flavours: dm2[0]; 3 flavours: dm2_21, dm2_31 (signed)          */
+  double theta[3];            /* 2 flavours: theta[0] = theta_v; 3 flavours: theta12, 13, 23 (rad) */
+  double rtol, atol;          /* DP45 error control (see xflat_evolve)                             */
+  double h0_km;               /* DP45 first trial step                                             */
+  double h_min_km, h_max_km;  /* DP45 step bounds (h_max_km <= 0: unbounded)                       */
+  double fixed_dr_km;         /* RK4 / LIE_RK4 target step; n = ceil((r1-r0)/fixed_dr) equal steps */
+  double rho0_gcc, r_ref_km, power, Ye;   /* XFLAT_MATTER_POWER_LAW                                */
+  double lambda_const_kmi;    /* XFLAT_MATTER_CONSTANT                                             */
+  void* cuda_stream;          /* cudaStream_t the handle works on (NULL = default stream)          */
+  uint64_t barrier_timeout_ns;/* limit of every device-wide wait (0 = 2 s)                         */
+  uint32_t block_size;        /* threads per block: 128, 256 or 512 (0 = library default)          */
+  uint32_t blocks_per_sm;     /* resident blocks per SM for the persistent grid (0 = occupancy)    */
+  uint32_t steps_per_launch;  /* radial steps per persistent launch in xflat_evolve (0 = 64)       */
+  uint32_t reserved1;
+} xflat_config;
+
+typedef struct xflat_s* xflat_t;
+
+typedef struct {
+  double r_km;                /* current radius of instance 0                                      */
+  double h_km;                /* last attempted step                                               */
+  double last_err;            /* last DP45 error norm (0 for fixed-step integrators)              */
+  uint64_t accepted, rejected;/* steps                                                             */
+  uint64_t stage_evals;       /* right-hand-side evaluations per beam (RK stages), incl. rejected  */
+  uint64_t beam_stage_updates;/* sum over instances of beams x stage_evals                         */
+  uint64_t launches;          /* persistent kernel launches issued                                */
+  uint32_t n_beams;           /* beams of instance 0                                               */
+  uint32_t n_instances;
+  int32_t status;             /* sticky device status (xflat_status) of instance 0                 */
+  uint32_t grid_blocks, block_size;
+} xflat_stats;
+
+/* ---- lifecycle ------------------------------------------------------------------------------- */
+
+/* Fill *cfg with defaults: 2 flavours, 64 x 32 bins, FP64, RK4, R = 11 km, E in [1, 60] MeV,
+ * dm2 = -2.4e-3 eV^2, theta_v = 0.1, no matter, rtol = atol = 1e-9, h0 = 1e-4 km, h_min = 1e-14 km. */
+int xflat_default_config(xflat_config* cfg);
+
+/* Create a solver for one bulb-model instance.  Validates cfg (XFLAT_ERR_INVAL on an out-of-range
+ * field), allocates the device state (two buffers of n_beams x n_comp values in the working
+ * precision), tables and barrier words on the current CUDA device.  *out is set only on success. */
+int xflat_create(const xflat_config* cfg, xflat_t* out);
+
+/* Create one solver holding n_inst independent instances (each with its own sizes, mixing,
+ * spectra, radius, step size and error control) that advance together in one persistent launch.
+ * All instances must share n_flavor, precision and integrator.  Instance i is addressed by the
+ * *_inst entry points; the plain entry points address instance 0. */
+int xflat_create_batch(const xflat_config* cfgs, uint32_t n_inst, xflat_t* out);
+
+/* Release every resource of the handle (synchronises its stream).  NULL is a no-op. */
+int xflat_destroy(xflat_t h);
+
+/* ---- inputs (Sec. 2 flux matrices; Sec. 3.2 discretisation) ----------------------------------- */
+
+/* Per-bin number luminosities N[species][flavor][k] = (L/<E>) f(E_k) dE in 1/s, species 0 = nu,
+ * 1 = nubar, flavour 0 = e, then x (2 flavours) or mu, tau (3 flavours; mu and tau must be equal).
+ * u_bins / u_weights (host, n_angle each) place the angle bins and weight them; both NULL = equal
+ * bins of [0,1] at midpoints with weight 1/n_angle.  Resets the state to the initial condition of
+ * Sec. 3.4 at r = R.  XFLAT_ERR_INVAL on non-finite input or u outside [0, 1). */
+int xflat_set_spectra(xflat_t h, const double* nnu, const double* u_bins, const double* u_weights);
+int xflat_set_spectra_inst(xflat_t h, uint32_t inst, const double* nnu, const double* u_bins,
+                           const double* u_weights);
+
+/* Put every beam of every instance back to the initial condition of Sec. 3.4 at radius r0_km. */
+int xflat_reset(xflat_t h, double r0_km);
+
+/* ---- evolution (Sec. 3.4: radial integration of Eq. eom) -------------------------------------- */
+
+/* Advance instance 0 (and every other instance, to the same r1) from its current radius to r1_km.
+ * r0_km must equal the current radius (set by xflat_reset / xflat_set_rho) to 1e-12 relative,
+ * else XFLAT_ERR_STATE.  Fixed-step integrators take n = ceil((r1-r0)/fixed_dr_km) equal steps,
+ * step m spanning [r0 + m h, r0 + (m+1) h].  DP45 attempts steps of size h (first h0_km, clipped
+ * to end exactly at r1), accepts a step when
+ *   Err = max_b ||e_b||_F / (atol + rtol max(||P~_b||_F, ||P~'_b||_F)) <= 1
+ * (e_b the embedded error matrix, P~ the traceless part) and continues with
+ * h * min(5, max(0.2, 0.9 Err^-1/5)) (at most h after a rejection), clipped to h_max_km.
+ * Returns the first device status that is not XFLAT_OK (TIMEOUT, NONFINITE, STEP). */
+int xflat_evolve(xflat_t h, double r0_km, double r1_km);
+
+/* Advance every unfinished instance i toward r1_km[i] (host array of n_inst), in one persistent
+ * launch per steps_per_launch steps, until all are finished or one fails. */
+int xflat_evolve_batch(xflat_t h, const double* r1_km_per_instance);
+
+/* Attempt at most max_steps radial steps of every unfinished instance toward r1_km[i] (NULL: the
+ * targets of the previous call) in ONE persistent launch.  When r1_km_per_instance is NULL and the
+ * previous call on the handle was also xflat_advance, the call only enqueues the launch (no host
+ * synchronisation, no copies), so a loop of advances measures the kernel alone.  *done_out
+ * (nullable, host) receives the all-finished flag as last read back from the device, which may lag
+ * one call behind; xflat_get_stats gives the exact state after synchronising. */
+int xflat_advance(xflat_t h, const double* r1_km_per_instance, uint32_t max_steps, int* done_out);
+
+/* ---- outputs ----------------------------------------------------------------------------------- */
+
+/* Traceless parts of the two beam-independent moments of the current state at the current radius:
+ *   J0 = sum_b du_j F_b / cos(theta_b),   J1 = sum_b du_j F_b,
+ * F_b the flux matrix of Sec. 2 (Eq. F: Phi_1 = R^2/(2 r^2) J0, Phi_c = R^2/(2 r^2) J1 up to their
+ * traces).  J0, J1: caller-owned host arrays of 2 n^2 doubles each (complex n x n, interleaved,
+ * row major), units of 1/s.  Computed by the device reduction (deterministic order). */
+int xflat_moments(xflat_t h, double* J0, double* J1);
+int xflat_moments_inst(xflat_t h, uint32_t inst, double* J0, double* J1);
+
+/* Copy the state of instance 0 (inst: instance inst) out in the given layout (double).  dst is a
+ * host pointer (dst_is_device = 0) or a device pointer on the handle's device (1) holding
+ * n_beams x 2 n^2 (MATRIX) or n_comp x n_beams (NATIVE) doubles. */
+int xflat_get_rho(xflat_t h, void* dst, int dst_is_device, int layout);
+int xflat_get_rho_inst(xflat_t h, uint32_t inst, void* dst, int dst_is_device, int layout);
+
+/* Replace the state of instance 0 (inst) and declare it to be at radius r_km (resume). */
+int xflat_set_rho(xflat_t h, const void* src, int src_is_device, int layout, double r_km);
+int xflat_set_rho_inst(xflat_t h, uint32_t inst, const void* src, int src_is_device, int layout,
+                       double r_km);
+
+/* Electron-flavour survival probability P_ee = |a_e|^2 (Sec. 3.4 validation figure): per beam
+ * (nullable host array of n_beams, nu and nubar) and the number-flux weighted mean over nu beams,
+ *   Pbar_ee = sum_{j,k} du_j N_nue,k P_ee(nu,j,k) / sum_{j,k} du_j N_nue,k   (nullable). */
+int xflat_pee(xflat_t h, double* pee_per_beam, double* pee_mean);
+int xflat_pee_inst(xflat_t h, uint32_t inst, double* pee_per_beam, double* pee_mean);
+
+int xflat_get_stats(xflat_t h, xflat_stats* out);
+int xflat_get_stats_inst(xflat_t h, uint32_t inst, xflat_stats* out);
+
+/* ---- adjoint (gradient of the final mean survival probability) -------------------------------- */
+
+/* Discrete adjoint of n_steps fixed RK4 steps (two flavours, FP64) from the initial condition of
+ * Sec. 3.4 at r0_km to r1_km, for the objective J = Pbar_ee(r1) of xflat_pee.  The forward pass
+ * stores the state every `checkpoint_every` steps and the backward pass recomputes each segment.
+ * Outputs (host, nullable):
+ *   dJ_dN     [2][n_flavor][n_energy]: dJ / d(per-bin number luminosity N of xflat_set_spectra)
+ *   dJ_dtheta : dJ / d(theta_v)
+ *   J_out     : the objective itself.
+ * Scale-factor gradients follow by the chain rule, e.g. dJ/dlog(L_nue) = sum_k N_e,k dJ_dN[0][0][k]. */
+int xflat_adjoint(xflat_t h, double r0_km, double r1_km, uint32_t n_steps, uint32_t checkpoint_every,
+                  double* dJ_dN, double* dJ_dtheta, double* J_out);
+
+/* ---- diagnostics ------------------------------------------------------------------------------- */
+
+const char* xflat_status_string(int status);
+const char* xflat_last_error(xflat_t h);
+
+/* Test hook: every device-wide barrier of the next launch waits for `extra` more arrivals than
+ * there are blocks, so it cannot complete; every block gives up after barrier_timeout_ns and the
+ * call returns XFLAT_ERR_TIMEOUT with the context intact.  0 restores normal operation. */
+int xflat_debug_barrier_extra(xflat_t h, uint32_t extra);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XFLAT_H */

@@ -1,0 +1,1016 @@
+// C ABI of the bulb-model solver: argument checks, tables, memory, launches (see include/xflat.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/xflat.h"
+#include "kernels.h"
+#include "xflat_internal.cuh"
+#include "step_kernel.cuh"
+
+using namespace xflat;
+
+namespace {
+
+// ---- physical constants (CODATA 2018 / SI 2019) ------------------------------------------------
+constexpr double kGF = 1.1663787e-5;                       // G_F / (hbar c)^3, GeV^-2
+constexpr double kHbarcEvKm = 197.3269804e6 * 1e-18;       // hbar c in eV km
+constexpr double kHbarcGevKm = 197.3269804e-3 * 1e-18;     // hbar c in GeV km
+constexpr double kCkms = 299792.458;                       // km / s
+constexpr double kMuG = 1.66053906660e-24;                 // atomic mass unit, g
+constexpr double kPi = 3.14159265358979323846;
+// sqrt(2) G_F (hbar c)^2: multiplies a number density in 1/km^3 to give 1/km
+const double kSqrt2GFhc2 = std::sqrt(2.0) * kGF * kHbarcGevKm * kHbarcGevKm;
+
+constexpr uint32_t kMaxJJ = 128;          // combined angle bins per piece (shared-memory table rows)
+constexpr uint32_t kAlignBeams = 4;       // instance offsets and piece starts: 16-byte vectors
+
+struct HostInst {
+  xflat_config cfg;
+  uint32_t n_beams = 0, n_pad = 0;
+  uint64_t off = 0;
+  std::vector<double> u, du;
+  std::vector<double> N;                  // [2][nf][ne]
+  bool spectra = false;
+  uint32_t e_off = 0, a_off = 0;
+};
+
+}  // namespace
+
+struct xflat_s {
+  std::vector<HostInst> inst;
+  int nf = 2, precision = 0, integrator = 0;
+  size_t real_size = 8;
+  int nc = 3;
+  cudaStream_t stream = nullptr;
+  int device = 0, sm_count = 0;
+  // device memory
+  void* planes = nullptr;                  // [2][nc][stride] Real
+  uint64_t stride = 0;
+  InstConst* d_ic = nullptr;
+  InstDyn* d_dyn = nullptr;
+  Piece* d_pieces = nullptr;
+  int* d_blk = nullptr;
+  unsigned long long* d_acc = nullptr;
+  unsigned long long* d_errmax = nullptr;
+  int* d_nonfinite = nullptr;
+  void* d_etab = nullptr;
+  double* d_u = nullptr;
+  double* d_du = nullptr;
+  Barrier* d_bar = nullptr;
+  int* d_words = nullptr;                  // [0] status, [1] all_done
+  int* h_words = nullptr;                  // pinned mirror
+  double* d_stage = nullptr;               // staging for conversions
+  size_t stage_bytes = 0;
+  // host mirrors
+  std::vector<InstConst> ic;
+  std::vector<InstDyn> dyn;
+  std::vector<Piece> pieces;
+  std::vector<int> blk;
+  const void* kernel = nullptr;
+  int block = 256, grid = 0;
+  size_t smem = 0;
+  int max_jj = 1;
+  uint64_t launches = 0;
+  uint32_t steps_per_launch = 64;
+  uint64_t timeout_ns = 2000000000ull;
+  uint32_t debug_extra = 0;
+  bool moments_valid = false;
+  bool advancing = false;                  // last call was an xflat_advance launch
+  std::string err;
+};
+
+namespace {
+
+int fail(xflat_t h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CUDA_TRY(h, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(h, XFLAT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+int check_config(const xflat_config& c, std::string& why) {
+  if (c.abi_version != XFLAT_ABI_VERSION) { why = "abi_version mismatch"; return XFLAT_ERR_INVAL; }
+  if (c.n_flavor != 2 && c.n_flavor != 3) { why = "n_flavor must be 2 or 3"; return XFLAT_ERR_INVAL; }
+  if (c.n_energy < 1 || c.n_angle < 1) { why = "n_energy and n_angle must be >= 1"; return XFLAT_ERR_INVAL; }
+  const uint64_t nb = 2ull * c.n_energy * c.n_angle;
+  if (nb >= (1ull << 31)) { why = "too many beams in one instance"; return XFLAT_ERR_INVAL; }
+  if (nb * (uint64_t)c.n_energy >= (1ull << 40)) { why = "n_beams * n_energy must be < 2^40"; return XFLAT_ERR_INVAL; }
+  if (c.precision > 1) { why = "precision must be FP64 or MIXED"; return XFLAT_ERR_INVAL; }
+  if (c.integrator > 2) { why = "unknown integrator"; return XFLAT_ERR_INVAL; }
+  if (c.integrator == XFLAT_LIE_RK4 && c.n_flavor != 2) { why = "LIE_RK4 is two-flavour only"; return XFLAT_ERR_UNSUPPORTED; }
+  if (c.matter_kind > 2) { why = "unknown matter_kind"; return XFLAT_ERR_INVAL; }
+  if (!(c.R_km > 0) || !is_fin(c.R_km)) { why = "R_km must be > 0"; return XFLAT_ERR_INVAL; }
+  if (!(c.E_min_MeV > 0) || !(c.E_max_MeV > c.E_min_MeV) || !is_fin(c.E_max_MeV)) { why = "need 0 < E_min < E_max"; return XFLAT_ERR_INVAL; }
+  for (int i = 0; i < 2; ++i) if (!is_fin(c.dm2_eV2[i])) { why = "dm2 not finite"; return XFLAT_ERR_INVAL; }
+  for (int i = 0; i < 3; ++i) if (!is_fin(c.theta[i])) { why = "theta not finite"; return XFLAT_ERR_INVAL; }
+  if (c.integrator == XFLAT_DP45) {
+    if (!(c.rtol >= 0) || !(c.atol >= 0) || !(c.rtol + c.atol > 0)) { why = "need rtol, atol >= 0, not both 0"; return XFLAT_ERR_INVAL; }
+    if (!(c.h0_km > 0) || !(c.h_min_km >= 0)) { why = "need h0 > 0 and h_min >= 0"; return XFLAT_ERR_INVAL; }
+  } else if (!(c.fixed_dr_km > 0)) { why = "fixed-step integrators need fixed_dr_km > 0"; return XFLAT_ERR_INVAL; }
+  if (c.matter_kind == XFLAT_MATTER_POWER_LAW &&
+      (!(c.rho0_gcc >= 0) || !(c.r_ref_km > 0) || !is_fin(c.power) || !(c.Ye >= 0))) {
+    why = "bad power-law matter parameters"; return XFLAT_ERR_INVAL;
+  }
+  if (c.matter_kind == XFLAT_MATTER_CONSTANT && !is_fin(c.lambda_const_kmi)) { why = "bad lambda_const"; return XFLAT_ERR_INVAL; }
+  if (c.block_size != 0 && c.block_size != 128 && c.block_size != 256 && c.block_size != 512) {
+    why = "block_size must be 0, 128, 256 or 512"; return XFLAT_ERR_INVAL;
+  }
+  return XFLAT_OK;
+}
+
+// Real three-flavour mixing U = R23 R13 R12 and the unit vacuum matrices U diag(0,1,0) U^T,
+// U diag(0,0,1) U^T (entries 00, 11, 22, 01, 02, 12).
+void vacuum_matrices_3f(const double th[3], double M21[6], double M31[6]) {
+  const double c12 = std::cos(th[0]), s12 = std::sin(th[0]);
+  const double c13 = std::cos(th[1]), s13 = std::sin(th[1]);
+  const double c23 = std::cos(th[2]), s23 = std::sin(th[2]);
+  const double R12[3][3] = {{c12, s12, 0}, {-s12, c12, 0}, {0, 0, 1}};
+  const double R13[3][3] = {{c13, 0, s13}, {0, 1, 0}, {-s13, 0, c13}};
+  const double R23[3][3] = {{1, 0, 0}, {0, c23, s23}, {0, -s23, c23}};
+  double T[3][3] = {}, U[3][3] = {};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int k = 0; k < 3; ++k) T[a][b] += R13[a][k] * R12[k][b];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int k = 0; k < 3; ++k) U[a][b] += R23[a][k] * T[k][b];
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+  for (int e = 0; e < 6; ++e) {
+    M21[e] = U[ia[e]][1] * U[ib[e]][1];
+    M31[e] = U[ia[e]][2] * U[ib[e]][2];
+  }
+}
+
+// ---- small device kernels (state set-up, conversions, observables) ---------------------------
+template <typename Real>
+__global__ void k_initial_state(Real* planes, uint64_t stride, uint64_t n_total, int nf) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_total) return;
+  const int nc = nf == 2 ? 3 : 9;
+  for (int b = 0; b < 2; ++b)
+    for (int c = 0; c < nc; ++c) {
+      Real v = 0;
+      if (nf == 2 && c == 2) v = 1;      // s = z: P = diag(1, 0)
+      if (nf == 3 && c == 0) v = 1;      // P = diag(1, 0, 0)
+      planes[((uint64_t)b * nc + c) * stride + i] = v;
+    }
+}
+
+// native (Real, internal convention) -> double dst in the requested layout
+template <typename Real>
+__global__ void k_export(const Real* src, uint64_t stride, uint32_t n, uint32_t n_nu, int nf, int layout,
+                         double* dst) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const bool bar = b >= n_nu;
+  if (layout == XFLAT_LAYOUT_NATIVE) {
+    const int nc = nf == 2 ? 3 : 9;
+    for (int c = 0; c < nc; ++c) dst[(uint64_t)c * n + b] = (double)src[(uint64_t)c * stride + b];
+    return;
+  }
+  double* m = dst + (uint64_t)b * 2 * nf * nf;
+  const double sg = bar ? -1.0 : 1.0;       // antineutrinos: the paper's Pbar = conj(internal)
+  if (nf == 2) {
+    const double sx = src[b], sy = src[stride + b], sz = src[2 * stride + b];
+    m[0] = 0.5 * (1 + sz); m[1] = 0;
+    m[2] = 0.5 * sx;       m[3] = -0.5 * sy * sg;
+    m[4] = 0.5 * sx;       m[5] = 0.5 * sy * sg;
+    m[6] = 0.5 * (1 - sz); m[7] = 0;
+  } else {
+    double v[9];
+    for (int c = 0; c < 9; ++c) v[c] = (double)src[(uint64_t)c * stride + b];
+    const double re[3][3] = {{v[0], v[3], v[5]}, {v[3], v[1], v[7]}, {v[5], v[7], v[2]}};
+    const double im[3][3] = {{0, v[4], v[6]}, {-v[4], 0, v[8]}, {-v[6], -v[8], 0}};
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) {
+        m[(a * 3 + c) * 2] = re[a][c];
+        m[(a * 3 + c) * 2 + 1] = sg * im[a][c];
+      }
+  }
+}
+
+template <typename Real>
+__global__ void k_import(const double* srcd, uint64_t stride, uint32_t n, uint32_t n_nu, int nf, int layout,
+                         Real* dst) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const bool bar = b >= n_nu;
+  if (layout == XFLAT_LAYOUT_NATIVE) {
+    const int nc = nf == 2 ? 3 : 9;
+    for (int c = 0; c < nc; ++c) dst[(uint64_t)c * stride + b] = (Real)srcd[(uint64_t)c * n + b];
+    return;
+  }
+  const double* m = srcd + (uint64_t)b * 2 * nf * nf;
+  const double sg = bar ? -1.0 : 1.0;
+  if (nf == 2) {
+    // P = (1 + s.sigma)/2: sx = 2 Re P01, sy = -2 Im P01, sz = P00 - P11 (nubar: conjugate first)
+    dst[b] = (Real)(2 * m[2]);
+    dst[stride + b] = (Real)(-2 * sg * m[3]);
+    dst[2 * stride + b] = (Real)(m[0] - m[6]);
+  } else {
+    const int d[3] = {0, 4, 8};
+    for (int a = 0; a < 3; ++a) dst[(uint64_t)a * stride + b] = (Real)m[d[a] * 2];
+    const int off[3] = {1, 2, 5};   // (0,1), (0,2), (1,2)
+    for (int e = 0; e < 3; ++e) {
+      dst[(uint64_t)(3 + 2 * e) * stride + b] = (Real)m[off[e] * 2];
+      dst[(uint64_t)(4 + 2 * e) * stride + b] = (Real)(sg * m[off[e] * 2 + 1]);
+    }
+  }
+}
+
+// P_ee per beam and the deterministic weighted mean over nu beams (one block, fixed tree).
+template <typename Real>
+__global__ void k_pee(const Real* src, uint64_t stride, uint32_t n, int nf, double* pee) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  pee[b] = nf == 2 ? 0.5 * (1.0 + (double)src[2 * stride + b]) : (double)src[b];
+}
+
+__global__ void k_pee_mean(const double* pee, const double* N_e, const double* du, uint32_t ne, uint32_t na,
+                           double* out) {
+  __shared__ double sn[1024], sd[1024];
+  double num = 0, den = 0;
+  const uint32_t nnu = ne * na;
+  for (uint32_t b = threadIdx.x; b < nnu; b += blockDim.x) {
+    const uint32_t j = b / ne, k = b % ne;
+    const double w = du[j] * N_e[k];
+    num += w * pee[b];
+    den += w;
+  }
+  sn[threadIdx.x] = num;
+  sd[threadIdx.x] = den;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) { sn[threadIdx.x] += sn[threadIdx.x + s]; sd[threadIdx.x] += sd[threadIdx.x + s]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sd[0] > 0 ? sn[0] / sd[0] : 0.0;
+}
+
+// ---- host helpers ------------------------------------------------------------------------------
+void build_tables(xflat_t h, HostInst& I, std::vector<double>& et, InstConst& ic) {
+  const xflat_config& c = I.cfg;
+  const uint32_t ne = c.n_energy, nf = c.n_flavor;
+  const double dE = (c.E_max_MeV - c.E_min_MeV) / ne;
+  const int ntab = nf == 2 ? 3 : 4;
+  et.assign((size_t)ntab * ne, 0.0);
+  // weight scale: total number luminosity of every listed species, flavour and bin
+  double S = 0;
+  for (double v : I.N) S += std::fabs(v);
+  const double wscale = S > 0 ? S : 1.0;
+  for (uint32_t k = 0; k < ne; ++k) {
+    const double E = c.E_min_MeV + (k + 0.5) * dE;
+    const double inv2E = 1.0 / (2.0 * E * 1e6 * kHbarcEvKm);     // 1/(2E) per eV^2, in 1/km
+    const double Ne = I.N[(0 * nf + 0) * ne + k], Nx = I.N[(0 * nf + 1) * ne + k];
+    const double Nbe = I.N[(1 * nf + 0) * ne + k], Nbx = I.N[(1 * nf + 1) * ne + k];
+    if (nf == 2) {
+      et[k] = c.dm2_eV2[0] * inv2E;
+      et[ne + k] = (Ne - Nx) / wscale;
+      et[2 * ne + k] = -(Nbe - Nbx) / wscale;
+    } else {
+      et[k] = c.dm2_eV2[0] * inv2E;
+      et[ne + k] = c.dm2_eV2[1] * inv2E;
+      et[2 * ne + k] = (Ne - Nx) / wscale;
+      et[3 * ne + k] = -(Nbe - Nbx) / wscale;
+    }
+  }
+  ic.wscale = wscale;
+  ic.mu_coef = kSqrt2GFhc2 * wscale / (4.0 * kPi * kCkms);
+  (void)h;
+}
+
+void fill_inst_const(HostInst& I, InstConst& ic) {
+  const xflat_config& c = I.cfg;
+  ic.beam_off = I.off;
+  ic.n_beams = I.n_beams;
+  ic.n_energy = c.n_energy;
+  ic.n_angle = c.n_angle;
+  ic.e_off = I.e_off;
+  ic.a_off = I.a_off;
+  ic.div_magic = (1ull << 40) / c.n_energy + 1;
+  ic.R2 = c.R_km * c.R_km;
+  ic.matter = (int)c.matter_kind;
+  ic.adaptive = c.integrator == XFLAT_DP45;
+  ic.r_ref = c.r_ref_km > 0 ? c.r_ref_km : 1.0;
+  ic.power = c.power;
+  ic.lam_coef = c.matter_kind == XFLAT_MATTER_POWER_LAW ? kSqrt2GFhc2 * c.Ye * c.rho0_gcc / kMuG * 1e15 : 0.0;
+  ic.lam_const = c.lambda_const_kmi;
+  ic.B[0] = std::sin(2 * c.theta[0]);
+  ic.B[1] = 0.0;
+  ic.B[2] = -std::cos(2 * c.theta[0]);
+  if (c.n_flavor == 3) vacuum_matrices_3f(c.theta, ic.M21, ic.M31);
+  ic.rtol = c.rtol;
+  ic.atol = c.atol;
+  ic.h_min = c.h_min_km;
+  ic.h_max = c.h_max_km > 0 ? c.h_max_km : INFINITY;
+}
+
+int upload_inst(xflat_t h) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_ic, h->ic.data(), sizeof(InstConst) * h->ic.size(), cudaMemcpyHostToDevice, h->stream));
+  return XFLAT_OK;
+}
+int upload_dyn(xflat_t h) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_dyn, h->dyn.data(), sizeof(InstDyn) * h->dyn.size(), cudaMemcpyHostToDevice, h->stream));
+  return XFLAT_OK;
+}
+int download_dyn(xflat_t h) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->dyn.data(), h->d_dyn, sizeof(InstDyn) * h->dyn.size(), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return XFLAT_OK;
+}
+
+int upload_tables(xflat_t h, uint32_t i) {
+  HostInst& I = h->inst[i];
+  std::vector<double> et;
+  build_tables(h, I, et, h->ic[i]);
+  const size_t n = et.size();
+  if (h->real_size == 8) {
+    CUDA_TRY(h, cudaMemcpy((double*)h->d_etab + I.e_off, et.data(), n * 8, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> ef(n);
+    for (size_t t = 0; t < n; ++t) ef[t] = (float)et[t];
+    CUDA_TRY(h, cudaMemcpy((float*)h->d_etab + I.e_off, ef.data(), n * 4, cudaMemcpyHostToDevice));
+  }
+  CUDA_TRY(h, cudaMemcpy(h->d_u + I.a_off, I.u.data(), I.u.size() * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(h, cudaMemcpy(h->d_du + I.a_off, I.du.data(), I.du.size() * 8, cudaMemcpyHostToDevice));
+  return XFLAT_OK;
+}
+
+void reset_dyn(xflat_t h, uint32_t i, double r0) {
+  InstDyn& d = h->dyn[i];
+  const xflat_config& c = h->inst[i].cfg;
+  std::memset(&d, 0, sizeof(InstDyn));
+  d.r = r0;
+  d.r_end = r0;
+  d.h = c.integrator == XFLAT_DP45 ? c.h0_km : c.fixed_dr_km;
+  d.done = 1;
+}
+
+// Cut all instances into G slices and slices into pieces; blk[b]..blk[b+1] are block b's pieces.
+void build_pieces(xflat_t h, int G) {
+  uint64_t T = 0;
+  for (auto& I : h->inst) T = std::max<uint64_t>(T, I.off + I.n_pad);
+  h->pieces.clear();
+  h->blk.assign(G + 1, 0);
+  h->max_jj = 1;
+  for (int b = 0; b < G; ++b) {
+    h->blk[b] = (int)h->pieces.size();
+    uint64_t s0 = (T * (uint64_t)b / G) / kAlignBeams * kAlignBeams;
+    uint64_t s1 = (b == G - 1) ? T : (T * (uint64_t)(b + 1) / G) / kAlignBeams * kAlignBeams;
+    for (uint32_t i = 0; i < h->inst.size(); ++i) {
+      const HostInst& I = h->inst[i];
+      const uint64_t lo = std::max<uint64_t>(s0, I.off), hi = std::min<uint64_t>(s1, I.off + I.n_beams);
+      if (lo >= hi) continue;
+      const uint32_t ne = I.cfg.n_energy;
+      const uint64_t maxlen = std::max<uint64_t>(kAlignBeams, ((uint64_t)(kMaxJJ - 1) * ne) / kAlignBeams * kAlignBeams);
+      for (uint64_t a = lo; a < hi; a += maxlen) {
+        const uint64_t e = std::min<uint64_t>(hi, a + maxlen);
+        Piece p{};
+        p.inst = (int)i;
+        p.start = (uint32_t)(a - I.off);
+        p.len = (uint32_t)(e - a);
+        p.jj_lo = p.start / ne;
+        p.n_jj = (p.start + p.len - 1) / ne - p.jj_lo + 1;
+        h->max_jj = std::max<int>(h->max_jj, (int)p.n_jj);
+        h->pieces.push_back(p);
+      }
+    }
+  }
+  h->blk[G] = (int)h->pieces.size();
+}
+
+size_t smem_bytes(size_t real_size, int max_jj) {
+  size_t s = 32 * kNMMax * sizeof(double);
+  s += (size_t)kMaxStages * max_jj * 2 * real_size;
+  s += (size_t)max_jj * real_size;
+  return (s + 15) / 16 * 16;
+}
+
+KParams make_params(xflat_t h, int n_steps, int init_only) {
+  KParams p{};
+  p.n_inst = (int)h->inst.size();
+  p.n_pieces = (int)h->pieces.size();
+  p.ic = h->d_ic;
+  p.dyn = h->d_dyn;
+  p.pieces = h->d_pieces;
+  p.blk_piece = h->d_blk;
+  p.acc = h->d_acc;
+  p.errmax = h->d_errmax;
+  p.nonfinite = h->d_nonfinite;
+  p.planeA = h->planes;
+  p.planeB = (char*)h->planes + (size_t)h->nc * h->stride * h->real_size;
+  p.plane_stride = h->stride;
+  p.etab = h->d_etab;
+  p.u_tab = h->d_u;
+  p.du_tab = h->d_du;
+  p.bar = h->d_bar;
+  p.timeout_ns = h->timeout_ns;
+  p.status = h->d_words;
+  p.all_done = h->d_words + 1;
+  p.n_steps = n_steps;
+  p.init_only = init_only;
+  p.max_jj = h->max_jj;
+  p.integrator = h->integrator;
+  return p;
+}
+
+int launch(xflat_t h, int n_steps, int init_only) {
+  KParams p = make_params(h, n_steps, init_only);
+  void* args[] = {&p};
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(h->grid);
+  cfg.blockDim = dim3(h->block);
+  cfg.dynamicSmemBytes = h->smem;
+  cfg.stream = h->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CUDA_TRY(h, cudaLaunchKernelExC(&cfg, h->kernel, args));
+  h->launches++;
+  return XFLAT_OK;
+}
+
+int clear_sync_words(xflat_t h) {
+  Barrier b{};
+  b.extra = h->debug_extra;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_bar, &b, sizeof(Barrier), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_words, 0, 2 * sizeof(int), h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_nonfinite, 0, h->inst.size() * sizeof(int), h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_errmax, 0, h->inst.size() * sizeof(unsigned long long), h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_acc, 0, h->inst.size() * kMaxStages * kNMMax * 2 * sizeof(unsigned long long), h->stream));
+  return XFLAT_OK;
+}
+
+int read_words(xflat_t h, int& status, int& all_done) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_words, h->d_words, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  status = h->h_words[0];
+  all_done = h->h_words[1];
+  return XFLAT_OK;
+}
+
+// Compute the moments of the current state of every instance (stage 1 constants).
+int refresh_moments(xflat_t h) {
+  std::vector<unsigned long long> evals(h->dyn.size());
+  for (size_t i = 0; i < h->dyn.size(); ++i) {
+    InstDyn& d = h->dyn[i];
+    evals[i] = d.stage_evals;
+    d.rs[1] = d.r;
+    d.xs[1] = h->ic[i].R2 / (d.r * d.r);
+    d.status = 0;
+    d.done = 0;            // the init pass skips finished instances
+  }
+  int rc = upload_dyn(h);
+  if (rc) return rc;
+  if ((rc = clear_sync_words(h))) return rc;
+  if ((rc = launch(h, 0, 1))) return rc;
+  if ((rc = download_dyn(h))) return rc;
+  int st, ad;
+  if ((rc = read_words(h, st, ad))) return rc;
+  for (size_t i = 0; i < h->dyn.size(); ++i) {
+    h->dyn[i].done = 1;
+    h->dyn[i].stage_evals = evals[i];   // an export is not an integration stage
+  }
+  if ((rc = upload_dyn(h))) return rc;
+  if (st) return fail(h, st, "device status after the moment reduction");
+  for (auto& d : h->dyn)
+    if (d.status) return fail(h, d.status, "non-finite moments");
+  h->moments_valid = true;
+  return XFLAT_OK;
+}
+
+int setup_launch_shape(xflat_t h, const xflat_config& c) {
+  h->kernel = step_kernel_ptr(h->nf, h->precision, h->integrator);
+  if (!h->kernel) return fail(h, XFLAT_ERR_UNSUPPORTED, "no kernel for this flavour/precision/integrator");
+  h->block = c.block_size ? (int)c.block_size : 256;
+  const size_t smax = smem_bytes(h->real_size, kMaxJJ);
+  CUDA_TRY(h, cudaFuncSetAttribute(h->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+  int occ = 0;
+  CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h->kernel, h->block, smax));
+  if (occ < 1) return fail(h, XFLAT_ERR_CUDA, "kernel does not fit on an SM");
+  if (c.blocks_per_sm) occ = std::min<int>(occ, (int)c.blocks_per_sm);
+  uint64_t T = 0;
+  for (auto& I : h->inst) T += I.n_pad;
+  int G = occ * h->sm_count;
+  // at least one vector of work per thread
+  const uint64_t per_block = (uint64_t)h->block * kAlignBeams;
+  G = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)G, (T + per_block - 1) / per_block));
+  h->grid = G;
+  build_pieces(h, G);
+  h->smem = smem_bytes(h->real_size, h->max_jj);
+  CUDA_TRY(h, cudaMalloc(&h->d_pieces, sizeof(Piece) * std::max<size_t>(1, h->pieces.size())));
+  CUDA_TRY(h, cudaMalloc(&h->d_blk, sizeof(int) * h->blk.size()));
+  CUDA_TRY(h, cudaMemcpy(h->d_pieces, h->pieces.data(), sizeof(Piece) * h->pieces.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(h, cudaMemcpy(h->d_blk, h->blk.data(), sizeof(int) * h->blk.size(), cudaMemcpyHostToDevice));
+  return XFLAT_OK;
+}
+
+int ensure_stage(xflat_t h, size_t bytes) {
+  if (h->stage_bytes >= bytes) return XFLAT_OK;
+  if (h->d_stage) cudaFree(h->d_stage);
+  h->d_stage = nullptr;
+  h->stage_bytes = 0;
+  CUDA_TRY(h, cudaMalloc(&h->d_stage, bytes));
+  h->stage_bytes = bytes;
+  return XFLAT_OK;
+}
+
+void* cur_plane(xflat_t h, uint32_t i) {
+  const int par = h->dyn[i].parity;
+  return (char*)h->planes + ((size_t)par * h->nc * h->stride + h->inst[i].off) * h->real_size;
+}
+
+int do_evolve(xflat_t h, const double* r1, bool sync_loop, uint32_t max_steps, int* done_out) {
+  int rc;
+  if (!sync_loop && r1 == nullptr && h->moments_valid && h->advancing) {
+    // continuing an advance: device state, moments and step geometry are already in place
+    if (done_out) *done_out = h->h_words[1];
+    if ((rc = launch(h, (int)max_steps, 0))) return rc;
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_words, h->d_words, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    return XFLAT_OK;
+  }
+  h->advancing = false;
+  if ((rc = download_dyn(h))) return rc;
+  bool any = false, changed = !h->moments_valid;
+  for (size_t i = 0; i < h->inst.size(); ++i) {
+    if (!h->inst[i].spectra) return fail(h, XFLAT_ERR_STATE, "set_spectra before evolve");
+    InstDyn& d = h->dyn[i];
+    const xflat_config& c = h->inst[i].cfg;
+    const double target = r1 ? r1[i] : d.r_end;
+    if (!is_fin(target)) return fail(h, XFLAT_ERR_INVAL, "non-finite target radius");
+    if (target < c.R_km) return fail(h, XFLAT_ERR_INVAL, "target radius below R");
+    d.status = 0;
+    if (r1 || d.r_end != target) {
+      changed = true;
+      d.r_end = target;
+      d.done = d.r >= target ? 1 : 0;
+      if (c.integrator != XFLAT_DP45) {
+        const double span = target - d.r;
+        long long n = (long long)std::ceil(span / c.fixed_dr_km - 1e-9);
+        if (n < 1) n = 1;
+        d.r0_fixed = d.r;
+        d.n_fixed = 0;
+        d.n_fixed_total = n;
+        d.h_fixed = span / (double)n;
+      } else {
+        d.last = 0;
+        if (!(d.h > 0)) d.h = c.h0_km;
+      }
+    }
+    d.rs[1] = d.r;
+    d.xs[1] = h->ic[i].R2 / (d.r * d.r);
+    any = any || !d.done;
+  }
+  if (done_out) *done_out = any ? 0 : 1;
+  if (!any) return XFLAT_OK;
+  if ((rc = upload_dyn(h))) return rc;
+  if ((rc = clear_sync_words(h))) return rc;
+  // moments of the current state and the first step's geometry, unless the previous launch left
+  // both in place (same targets, state untouched since)
+  if (changed && (rc = launch(h, 0, 1))) return rc;
+  if (!sync_loop) {
+    if ((rc = launch(h, (int)max_steps, 0))) return rc;
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_words, h->d_words, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    // the step kernel keeps the moments of the current state (stage 1) up to date
+    h->moments_valid = true;
+    h->advancing = true;
+    return XFLAT_OK;
+  }
+  for (;;) {
+    if ((rc = launch(h, (int)h->steps_per_launch, 0))) return rc;
+    int st, ad;
+    if ((rc = read_words(h, st, ad))) return rc;
+    if (st || ad) break;
+  }
+  if ((rc = download_dyn(h))) return rc;
+  h->moments_valid = true;
+  int st, ad;
+  if ((rc = read_words(h, st, ad))) return rc;
+  for (auto& d : h->dyn)
+    if (d.status) return fail(h, d.status, std::string("device status: ") + xflat_status_string(d.status));
+  if (st) return fail(h, st, std::string("device status: ") + xflat_status_string(st));
+  return XFLAT_OK;
+}
+
+int create_impl(const xflat_config* cfgs, uint32_t n, xflat_t* out) {
+  if (!cfgs || !out || n == 0) return XFLAT_ERR_INVAL;
+  std::string why;
+  for (uint32_t i = 0; i < n; ++i) {
+    int rc = check_config(cfgs[i], why);
+    if (rc) { (void)why; return rc; }
+    if (cfgs[i].n_flavor != cfgs[0].n_flavor || cfgs[i].precision != cfgs[0].precision ||
+        cfgs[i].integrator != cfgs[0].integrator)
+      return XFLAT_ERR_INVAL;
+  }
+  xflat_t h = new (std::nothrow) xflat_s();
+  if (!h) return XFLAT_ERR_NOMEM;
+  auto bail = [&](int rc) { xflat_destroy(h); return rc; };
+  h->nf = (int)cfgs[0].n_flavor;
+  h->precision = (int)cfgs[0].precision;
+  h->integrator = (int)cfgs[0].integrator;
+  h->real_size = h->precision == XFLAT_FP64 ? 8 : 4;
+  h->nc = h->nf == 2 ? 3 : 9;
+  h->stream = (cudaStream_t)cfgs[0].cuda_stream;
+  h->timeout_ns = cfgs[0].barrier_timeout_ns ? cfgs[0].barrier_timeout_ns : 2000000000ull;
+  h->steps_per_launch = cfgs[0].steps_per_launch ? cfgs[0].steps_per_launch : 64;
+  if (cudaGetDevice(&h->device) != cudaSuccess) return bail(XFLAT_ERR_CUDA);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return bail(XFLAT_ERR_CUDA);
+  if (prop.major * 10 + prop.minor != 103) return bail(XFLAT_ERR_CUDA);
+  h->sm_count = prop.multiProcessorCount;
+  // layout
+  h->inst.resize(n);
+  uint64_t off = 0;
+  uint32_t eoff = 0, aoff = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    HostInst& I = h->inst[i];
+    I.cfg = cfgs[i];
+    I.n_beams = 2u * I.cfg.n_energy * I.cfg.n_angle;
+    I.n_pad = (I.n_beams + kAlignBeams - 1) / kAlignBeams * kAlignBeams;
+    I.off = off;
+    off += I.n_pad;
+    I.e_off = eoff;
+    eoff += (h->nf == 2 ? 3 : 4) * I.cfg.n_energy;
+    I.a_off = aoff;
+    aoff += I.cfg.n_angle;
+    I.u.resize(I.cfg.n_angle);
+    I.du.resize(I.cfg.n_angle);
+    for (uint32_t j = 0; j < I.cfg.n_angle; ++j) {
+      I.u[j] = (j + 0.5) / I.cfg.n_angle;
+      I.du[j] = 1.0 / I.cfg.n_angle;
+    }
+    I.N.assign(2ull * h->nf * I.cfg.n_energy, 0.0);
+  }
+  h->stride = (off + 63) / 64 * 64;
+  const size_t plane_bytes = 2ull * h->nc * h->stride * h->real_size;
+  if (cudaMalloc(&h->planes, plane_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
+  if (cudaMalloc(&h->d_ic, sizeof(InstConst) * n) != cudaSuccess ||
+      cudaMalloc(&h->d_dyn, sizeof(InstDyn) * n) != cudaSuccess ||
+      cudaMalloc(&h->d_acc, sizeof(unsigned long long) * n * kMaxStages * kNMMax * 2) != cudaSuccess ||
+      cudaMalloc(&h->d_errmax, sizeof(unsigned long long) * n) != cudaSuccess ||
+      cudaMalloc(&h->d_nonfinite, sizeof(int) * n) != cudaSuccess ||
+      cudaMalloc(&h->d_etab, (size_t)eoff * h->real_size) != cudaSuccess ||
+      cudaMalloc(&h->d_u, sizeof(double) * aoff) != cudaSuccess ||
+      cudaMalloc(&h->d_du, sizeof(double) * aoff) != cudaSuccess ||
+      cudaMalloc(&h->d_bar, sizeof(Barrier)) != cudaSuccess ||
+      cudaMalloc(&h->d_words, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&h->h_words, 2 * sizeof(int)) != cudaSuccess)
+    return bail(XFLAT_ERR_NOMEM);
+  cudaMemset(h->d_etab, 0, (size_t)eoff * h->real_size);
+  h->ic.assign(n, InstConst{});
+  h->dyn.assign(n, InstDyn{});
+  for (uint32_t i = 0; i < n; ++i) {
+    fill_inst_const(h->inst[i], h->ic[i]);
+    h->ic[i].wscale = 1.0;
+    h->ic[i].mu_coef = 0.0;
+    reset_dyn(h, i, h->inst[i].cfg.R_km);
+  }
+  int rc = setup_launch_shape(h, cfgs[0]);
+  if (rc) return bail(rc);
+  if ((rc = upload_inst(h)) || (rc = upload_dyn(h))) return bail(rc);
+  const uint64_t tot = h->stride;
+  if (h->real_size == 8) k_initial_state<double><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>((double*)h->planes, h->stride, tot, h->nf);
+  else k_initial_state<float><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>((float*)h->planes, h->stride, tot, h->nf);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(XFLAT_ERR_CUDA);
+  *out = h;
+  return XFLAT_OK;
+}
+
+}  // namespace
+
+// ==== exported C ABI ============================================================================
+extern "C" {
+
+int xflat_default_config(xflat_config* c) {
+  if (!c) return XFLAT_ERR_INVAL;
+  std::memset(c, 0, sizeof(*c));
+  c->abi_version = XFLAT_ABI_VERSION;
+  c->n_flavor = 2;
+  c->n_energy = 64;
+  c->n_angle = 32;
+  c->precision = XFLAT_FP64;
+  c->integrator = XFLAT_RK4;
+  c->matter_kind = XFLAT_MATTER_NONE;
+  c->R_km = 11.0;
+  c->E_min_MeV = 1.0;
+  c->E_max_MeV = 60.0;
+  c->dm2_eV2[0] = -2.4e-3;
+  c->theta[0] = 0.1;
+  c->rtol = 1e-9;
+  c->atol = 1e-9;
+  c->h0_km = 1e-4;
+  c->h_min_km = 1e-14;
+  c->h_max_km = 0.0;
+  c->fixed_dr_km = 0.0945;
+  c->rho0_gcc = 1e7;
+  c->r_ref_km = 100.0;
+  c->power = 3.0;
+  c->Ye = 0.5;
+  return XFLAT_OK;
+}
+
+int xflat_create(const xflat_config* cfg, xflat_t* out) { return create_impl(cfg, 1, out); }
+
+int xflat_create_batch(const xflat_config* cfgs, uint32_t n_inst, xflat_t* out) {
+  return create_impl(cfgs, n_inst, out);
+}
+
+int xflat_destroy(xflat_t h) {
+  if (!h) return XFLAT_OK;
+  if (h->stream || true) cudaStreamSynchronize(h->stream);
+  void* ptrs[] = {h->planes, h->d_ic, h->d_dyn, h->d_pieces, h->d_blk, h->d_acc, h->d_errmax,
+                  h->d_nonfinite, h->d_etab, h->d_u, h->d_du, h->d_bar, h->d_words, h->d_stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->h_words) cudaFreeHost(h->h_words);
+  delete h;
+  return XFLAT_OK;
+}
+
+int xflat_set_spectra_inst(xflat_t h, uint32_t inst, const double* nnu, const double* u_bins,
+                           const double* u_weights) {
+  if (!h) return XFLAT_ERR_INVAL;
+  if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
+  if (!nnu) return fail(h, XFLAT_ERR_INVAL, "nnu is NULL");
+  if ((u_bins == nullptr) != (u_weights == nullptr)) return fail(h, XFLAT_ERR_INVAL, "u_bins and u_weights go together");
+  HostInst& I = h->inst[inst];
+  const uint32_t ne = I.cfg.n_energy, na = I.cfg.n_angle, nf = I.cfg.n_flavor;
+  std::vector<double> N(nnu, nnu + 2ull * nf * ne);
+  for (double v : N)
+    if (!is_fin(v)) return fail(h, XFLAT_ERR_INVAL, "non-finite luminosity");
+  if (nf == 3)
+    for (int s = 0; s < 2; ++s)
+      for (uint32_t k = 0; k < ne; ++k)
+        if (N[(s * 3 + 1) * ne + k] != N[(s * 3 + 2) * ne + k])
+          return fail(h, XFLAT_ERR_INVAL, "mu and tau spectra must be equal");
+  if (u_bins) {
+    for (uint32_t j = 0; j < na; ++j) {
+      if (!(u_bins[j] >= 0.0 && u_bins[j] < 1.0)) return fail(h, XFLAT_ERR_INVAL, "u outside [0, 1)");
+      if (!is_fin(u_weights[j]) || u_weights[j] < 0) return fail(h, XFLAT_ERR_INVAL, "bad u weight");
+    }
+    I.u.assign(u_bins, u_bins + na);
+    I.du.assign(u_weights, u_weights + na);
+  }
+  I.N = N;
+  I.spectra = true;
+  int rc;
+  if ((rc = download_dyn(h))) return rc;
+  fill_inst_const(I, h->ic[inst]);
+  if ((rc = upload_tables(h, inst))) return rc;
+  if ((rc = upload_inst(h))) return rc;
+  reset_dyn(h, inst, I.cfg.R_km);
+  if ((rc = upload_dyn(h))) return rc;
+  // initial condition of this instance in both buffers (the kernel writes both)
+  const size_t nb = I.n_pad;
+  if (h->real_size == 8)
+    k_initial_state<double><<<(unsigned)((nb + 255) / 256), 256, 0, h->stream>>>((double*)h->planes + I.off, h->stride, nb, h->nf);
+  else
+    k_initial_state<float><<<(unsigned)((nb + 255) / 256), 256, 0, h->stream>>>((float*)h->planes + I.off, h->stride, nb, h->nf);
+  CUDA_TRY(h, cudaGetLastError());
+  h->moments_valid = false;
+  return XFLAT_OK;
+}
+
+int xflat_set_spectra(xflat_t h, const double* nnu, const double* u_bins, const double* u_weights) {
+  return xflat_set_spectra_inst(h, 0, nnu, u_bins, u_weights);
+}
+
+int xflat_reset(xflat_t h, double r0_km) {
+  if (!h) return XFLAT_ERR_INVAL;
+  if (!is_fin(r0_km)) return fail(h, XFLAT_ERR_INVAL, "r0 not finite");
+  int rc;
+  for (size_t i = 0; i < h->inst.size(); ++i) {
+    if (r0_km < h->inst[i].cfg.R_km) return fail(h, XFLAT_ERR_INVAL, "r0 below R");
+    reset_dyn(h, (uint32_t)i, r0_km);
+  }
+  const uint64_t tot = h->stride;
+  if (h->real_size == 8) k_initial_state<double><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>((double*)h->planes, h->stride, tot, h->nf);
+  else k_initial_state<float><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>((float*)h->planes, h->stride, tot, h->nf);
+  CUDA_TRY(h, cudaGetLastError());
+  if ((rc = upload_dyn(h))) return rc;
+  h->moments_valid = false;
+  return XFLAT_OK;
+}
+
+int xflat_evolve_batch(xflat_t h, const double* r1) {
+  if (!h || !r1) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
+  return do_evolve(h, r1, true, 0, nullptr);
+}
+
+int xflat_evolve(xflat_t h, double r0_km, double r1_km) {
+  if (!h) return XFLAT_ERR_INVAL;
+  int rc;
+  if ((rc = download_dyn(h))) return rc;
+  const double r = h->dyn[0].r;
+  if (!is_fin(r0_km) || std::fabs(r0_km - r) > 1e-12 * std::max(1.0, std::fabs(r)))
+    return fail(h, XFLAT_ERR_STATE, "r0 does not match the current radius");
+  if (!(r1_km >= r0_km)) return fail(h, XFLAT_ERR_INVAL, "need r1 >= r0");
+  std::vector<double> t(h->inst.size(), r1_km);
+  return do_evolve(h, t.data(), true, 0, nullptr);
+}
+
+int xflat_advance(xflat_t h, const double* r1, uint32_t max_steps, int* done_out) {
+  if (!h) return XFLAT_ERR_INVAL;
+  if (max_steps == 0) return fail(h, XFLAT_ERR_INVAL, "max_steps must be >= 1");
+  return do_evolve(h, r1, false, max_steps, done_out);
+}
+
+int xflat_moments_inst(xflat_t h, uint32_t inst, double* J0, double* J1) {
+  if (!h || !J0 || !J1) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
+  if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
+  if (!h->inst[inst].spectra) return fail(h, XFLAT_ERR_STATE, "set_spectra first");
+  int rc;
+  if ((rc = download_dyn(h))) return rc;
+  if (!h->moments_valid && (rc = refresh_moments(h))) return rc;
+  const InstDyn& d = h->dyn[inst];
+  const double ws = h->ic[inst].wscale;
+  const int nf = h->nf;
+  for (int t = 0; t < 2; ++t) {
+    const double* m = d.mom[1] + t * (nf == 2 ? 3 : 9);
+    double* J = t == 0 ? J0 : J1;
+    std::memset(J, 0, sizeof(double) * 2 * nf * nf);
+    if (nf == 2) {
+      J[0] = 0.5 * ws * m[2];
+      J[2] = 0.5 * ws * m[0];
+      J[3] = -0.5 * ws * m[1];
+      J[4] = 0.5 * ws * m[0];
+      J[5] = 0.5 * ws * m[1];
+      J[6] = -0.5 * ws * m[2];
+    } else {
+      const double tr = (m[0] + m[1] + m[2]) / 3.0;
+      const double re[3][3] = {{m[0] - tr, m[3], m[5]}, {m[3], m[1] - tr, m[7]}, {m[5], m[7], m[2] - tr}};
+      const double im[3][3] = {{0, m[4], m[6]}, {-m[4], 0, m[8]}, {-m[6], -m[8], 0}};
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+          J[(a * 3 + c) * 2] = ws * re[a][c];
+          J[(a * 3 + c) * 2 + 1] = ws * im[a][c];
+        }
+    }
+  }
+  return XFLAT_OK;
+}
+
+int xflat_moments(xflat_t h, double* J0, double* J1) { return xflat_moments_inst(h, 0, J0, J1); }
+
+int xflat_get_rho_inst(xflat_t h, uint32_t inst, void* dst, int dst_is_device, int layout) {
+  if (!h || !dst) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
+  if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
+  if (layout != XFLAT_LAYOUT_MATRIX && layout != XFLAT_LAYOUT_NATIVE) return fail(h, XFLAT_ERR_INVAL, "bad layout");
+  int rc;
+  if ((rc = download_dyn(h))) return rc;
+  const HostInst& I = h->inst[inst];
+  const uint32_t n = I.n_beams, n_nu = n / 2;
+  const size_t bytes = layout == XFLAT_LAYOUT_MATRIX ? (size_t)n * 2 * h->nf * h->nf * 8 : (size_t)n * h->nc * 8;
+  double* target = (double*)dst;
+  if (!dst_is_device) {
+    if ((rc = ensure_stage(h, bytes))) return rc;
+    target = h->d_stage;
+  }
+  const void* src = cur_plane(h, inst);
+  const unsigned nb = (n + 255) / 256;
+  if (h->real_size == 8) k_export<double><<<nb, 256, 0, h->stream>>>((const double*)src, h->stride, n, n_nu, h->nf, layout, target);
+  else k_export<float><<<nb, 256, 0, h->stream>>>((const float*)src, h->stride, n, n_nu, h->nf, layout, target);
+  CUDA_TRY(h, cudaGetLastError());
+  if (!dst_is_device) CUDA_TRY(h, cudaMemcpyAsync(dst, target, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return XFLAT_OK;
+}
+
+int xflat_get_rho(xflat_t h, void* dst, int dst_is_device, int layout) {
+  return xflat_get_rho_inst(h, 0, dst, dst_is_device, layout);
+}
+
+int xflat_set_rho_inst(xflat_t h, uint32_t inst, const void* src, int src_is_device, int layout, double r_km) {
+  if (!h || !src) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
+  if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
+  if (layout != XFLAT_LAYOUT_MATRIX && layout != XFLAT_LAYOUT_NATIVE) return fail(h, XFLAT_ERR_INVAL, "bad layout");
+  if (!is_fin(r_km) || r_km < h->inst[inst].cfg.R_km) return fail(h, XFLAT_ERR_INVAL, "radius below R or not finite");
+  int rc;
+  if ((rc = download_dyn(h))) return rc;
+  const HostInst& I = h->inst[inst];
+  const uint32_t n = I.n_beams, n_nu = n / 2;
+  const size_t bytes = layout == XFLAT_LAYOUT_MATRIX ? (size_t)n * 2 * h->nf * h->nf * 8 : (size_t)n * h->nc * 8;
+  const double* from = (const double*)src;
+  if (!src_is_device) {
+    if ((rc = ensure_stage(h, bytes))) return rc;
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_stage, src, bytes, cudaMemcpyHostToDevice, h->stream));
+    from = h->d_stage;
+  }
+  void* dstp = cur_plane(h, inst);
+  const unsigned nb = (n + 255) / 256;
+  if (h->real_size == 8) k_import<double><<<nb, 256, 0, h->stream>>>(from, h->stride, n, n_nu, h->nf, layout, (double*)dstp);
+  else k_import<float><<<nb, 256, 0, h->stream>>>(from, h->stride, n, n_nu, h->nf, layout, (float*)dstp);
+  CUDA_TRY(h, cudaGetLastError());
+  InstDyn& d = h->dyn[inst];
+  d.r = r_km;
+  d.r_end = r_km;
+  d.done = 1;
+  d.status = 0;
+  if ((rc = upload_dyn(h))) return rc;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->moments_valid = false;
+  return XFLAT_OK;
+}
+
+int xflat_set_rho(xflat_t h, const void* src, int src_is_device, int layout, double r_km) {
+  return xflat_set_rho_inst(h, 0, src, src_is_device, layout, r_km);
+}
+
+int xflat_pee_inst(xflat_t h, uint32_t inst, double* pee_per_beam, double* pee_mean) {
+  if (!h) return XFLAT_ERR_INVAL;
+  if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
+  int rc;
+  if ((rc = download_dyn(h))) return rc;
+  const HostInst& I = h->inst[inst];
+  const uint32_t n = I.n_beams, ne = I.cfg.n_energy, na = I.cfg.n_angle;
+  const size_t need = ((size_t)n + ne + 2) * 8;
+  if ((rc = ensure_stage(h, need))) return rc;
+  double* pee = h->d_stage;
+  double* Ne = pee + n;
+  double* mean = Ne + ne;
+  const void* src = cur_plane(h, inst);
+  const unsigned nb = (n + 255) / 256;
+  if (h->real_size == 8) k_pee<double><<<nb, 256, 0, h->stream>>>((const double*)src, h->stride, n, h->nf, pee);
+  else k_pee<float><<<nb, 256, 0, h->stream>>>((const float*)src, h->stride, n, h->nf, pee);
+  CUDA_TRY(h, cudaMemcpyAsync(Ne, I.N.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, h->stream));
+  k_pee_mean<<<1, 1024, 0, h->stream>>>(pee, Ne, h->d_du + I.a_off, ne, na, mean);
+  CUDA_TRY(h, cudaGetLastError());
+  if (pee_per_beam) CUDA_TRY(h, cudaMemcpyAsync(pee_per_beam, pee, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  if (pee_mean) CUDA_TRY(h, cudaMemcpyAsync(pee_mean, mean, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return XFLAT_OK;
+}
+
+int xflat_pee(xflat_t h, double* pee_per_beam, double* pee_mean) {
+  return xflat_pee_inst(h, 0, pee_per_beam, pee_mean);
+}
+
+int xflat_get_stats_inst(xflat_t h, uint32_t inst, xflat_stats* out) {
+  if (!h || !out) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
+  if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
+  int rc;
+  if ((rc = download_dyn(h))) return rc;
+  std::memset(out, 0, sizeof(*out));
+  const InstDyn& d = h->dyn[inst];
+  out->r_km = d.r;
+  out->h_km = h->inst[inst].cfg.integrator == XFLAT_DP45 ? d.h : d.h_fixed;
+  out->last_err = d.err;
+  out->accepted = d.accepted;
+  out->rejected = d.rejected;
+  out->stage_evals = d.stage_evals;
+  uint64_t bsu = 0;
+  for (size_t i = 0; i < h->inst.size(); ++i) bsu += (uint64_t)h->inst[i].n_beams * h->dyn[i].stage_evals;
+  out->beam_stage_updates = bsu;
+  out->launches = h->launches;
+  out->n_beams = h->inst[inst].n_beams;
+  out->n_instances = (uint32_t)h->inst.size();
+  out->status = d.status;
+  out->grid_blocks = (uint32_t)h->grid;
+  out->block_size = (uint32_t)h->block;
+  return XFLAT_OK;
+}
+
+int xflat_get_stats(xflat_t h, xflat_stats* out) { return xflat_get_stats_inst(h, 0, out); }
+
+int xflat_adjoint(xflat_t h, double, double, uint32_t, uint32_t, double*, double*, double*) {
+  return fail(h, XFLAT_ERR_UNSUPPORTED, "adjoint not built");
+}
+
+const char* xflat_status_string(int s) {
+  switch (s) {
+    case XFLAT_OK: return "ok";
+    case XFLAT_ERR_INVAL: return "invalid argument";
+    case XFLAT_ERR_NOMEM: return "out of memory";
+    case XFLAT_ERR_CUDA: return "CUDA error";
+    case XFLAT_ERR_TIMEOUT: return "device barrier timeout";
+    case XFLAT_ERR_NONFINITE: return "non-finite value";
+    case XFLAT_ERR_STEP: return "step size underflow";
+    case XFLAT_ERR_STATE: return "call order violated";
+    case XFLAT_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* xflat_last_error(xflat_t h) { return h ? h->err.c_str() : "NULL handle"; }
+
+int xflat_debug_barrier_extra(xflat_t h, uint32_t extra) {
+  if (!h) return XFLAT_ERR_INVAL;
+  h->debug_extra = extra;
+  return XFLAT_OK;
+}
+
+}  // extern "C"

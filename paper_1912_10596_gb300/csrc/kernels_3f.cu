@@ -1,0 +1,22 @@
+// Three-flavour step kernels (3x3 Hermitian density matrices): FP64 and mixed, RK4 / DP45.
+#include "step_kernel.cuh"
+#include "kernels.h"
+
+namespace xflat {
+
+const void* step_kernel_ptr_2f(int precision, int integrator);
+
+const void* step_kernel_ptr(int n_flavor, int precision, int integrator) {
+  if (n_flavor == 2) return step_kernel_ptr_2f(precision, integrator);
+  if (n_flavor != 3) return nullptr;
+  if (precision == 0) {
+    if (integrator == kRK4) return (const void*)&step_kernel<Phys3<double>, TabRK4, double, false>;
+    if (integrator == kDP45) return (const void*)&step_kernel<Phys3<double>, TabDP45, double, false>;
+  } else {
+    if (integrator == kRK4) return (const void*)&step_kernel<Phys3<float>, TabRK4, float, false>;
+    if (integrator == kDP45) return (const void*)&step_kernel<Phys3<float>, TabDP45, float, false>;
+  }
+  return nullptr;
+}
+
+}  // namespace xflat
