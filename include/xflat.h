@@ -227,6 +227,37 @@ int xflat_get_stats_inst(xflat_t h, uint32_t inst, xflat_stats* out);
 int xflat_adjoint(xflat_t h, double r0_km, double r1_km, uint32_t n_steps, uint32_t checkpoint_every,
                   double* dJ_dN, double* dJ_dtheta, double* J_out);
 
+/* ---- allocation-free moments (the paper has no counterpart: an addition for callers) ------------ */
+
+#define XFLAT_NOALLOC_MAX_ANGLES 4096u
+
+/* The two moments J0, J1 of xflat_moments for a two-flavour state supplied by the caller, computed
+ * without allocating any memory: for callers that cannot call cudaMalloc at that point -- a host
+ * framework that owns the device memory pool through its own allocator, or a time-critical loop
+ * that must not stall, since cudaMalloc/cudaFree can synchronise the device and can fail when
+ * memory is short.  No handle is needed and nothing is allocated: the inputs and the output are
+ * caller-owned device memory, and the only scratch (two rows of six doubles per angle bin and a
+ * counter, 393 KB in all) is a fixed array that every GPU which loads the library holds until the
+ * process exits.
+ *   d_state   [3][2 n_angle n_energy] double: Bloch planes in XFLAT_LAYOUT_NATIVE order (beam
+ *             index as above; antineutrino beams hold the vector of conj(Pbar))
+ *   d_g       [2][n_energy] double: signed per-bin weights, nu: N_e,k - N_x,k; nubar:
+ *             -(Nbar_e,k - Nbar_x,k), in 1/s
+ *   d_u, d_du [n_angle] double: angle-bin positions u_j in [0, 1) and weights du_j
+ *   R_km, r_km: neutrino-sphere radius and the radius at which cos(theta) is evaluated (r >= R)
+ *   d_J       [6] double out: Bloch vectors j0 then j1, with J = (1/2) j.sigma, units of 1/s
+ *   cuda_stream: cudaStream_t for the work (NULL = default stream)
+ * Returns XFLAT_ERR_INVAL for NULL pointers, empty sizes, r < R or n_angle >
+ * XFLAT_NOALLOC_MAX_ANGLES (the scratch has no room for more rows), XFLAT_ERR_CUDA if a launch
+ * fails.  The work is only enqueued: synchronise the stream before reading d_J.
+ * The first call on a device (with that device current) looks up the device address of the
+ * scratch array; make that first call before any stream capture.  Every call on a device shares
+ * the one scratch array: calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and give wrong results; serialise them. */
+int xflat_moments_2f_noalloc(const double* d_state, uint32_t n_energy, uint32_t n_angle,
+                             const double* d_g, const double* d_u, const double* d_du, double R_km,
+                             double r_km, double* d_J, void* cuda_stream);
+
 /* ---- diagnostics ------------------------------------------------------------------------------- */
 
 const char* xflat_status_string(int status);
