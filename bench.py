@@ -95,12 +95,18 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
-def time_device_steps(xf, torch, wl, precision, steps, warmup, flush):
+def bench_config(xf, wl, precision):
+    return xf.config_from_workload(wl, precision=precision, steps_per_launch=1,
+                                   rtol=1e-6 if precision == "mixed" else 1e-9,
+                                   atol=1e-6 if precision == "mixed" else 1e-9)
+
+
+def time_device_steps(xf, torch, wl, precision, steps, warmup, flush, shape=None):
     """Return (ms per step, beam-stage updates per step, stats) for `steps` timed single-step launches."""
     stream = torch.cuda.current_stream()
-    cfg = xf.config_from_workload(wl, precision=precision, steps_per_launch=1,
-                                  rtol=1e-6 if precision == "mixed" else 1e-9,
-                                  atol=1e-6 if precision == "mixed" else 1e-9)
+    cfg = bench_config(xf, wl, precision)
+    if shape is not None:
+        cfg.block_size, cfg.blocks_per_sm = shape
     cfg.cuda_stream = stream.cuda_stream
     s = xf.Solver(cfg)
     s.set_spectra(wl.spectra())
@@ -180,6 +186,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -222,11 +229,16 @@ def main():
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     flush = lambda: flush_l2(flush_buf)  # noqa: E731
 
+    shape = None
+    if not args.no_tune:
+        from paper_1912_10596_gb300 import autotune
+        shape = autotune.tune(xf, [bench_config(xf, wl, "mixed")], [wl.spectra()], [wl.r1],
+                              log=lambda m: print(m, file=sys.stderr))
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        ms, bsu, st, solver = time_device_steps(xf, torch, wl, "mixed", args.steps, args.warmup, flush)
+        ms, bsu, st, solver = time_device_steps(xf, torch, wl, "mixed", args.steps, args.warmup, flush, shape)
     clocks = clk.summary()
     t_ms = sum(ms)
     if world > 1:
@@ -265,7 +277,8 @@ def main():
             "config": {"workload": wl.name, "beams": wl.n_beams, "integrator": "dp45",
                        "precision": "mixed", "r_start_km": 11.0, "stage_evals_per_step": bsu / wl.n_beams,
                        "l2": "flushed between timed steps (write of a 258 MB buffer)",
-                       "grid_blocks": st.grid_blocks, "block_size": st.block_size},
+                       "grid_blocks": st.grid_blocks, "block_size": st.block_size,
+                       "autotuned_shape": list(shape) if shape else None},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None,
                          "note": f"{BYTES_PER_BEAM_STAGE[('mixed', 'dp45')]} algorithmic B per beam-stage; peak {peak_kind}"},

@@ -268,6 +268,14 @@ const char* xflat_last_error(xflat_t h);
  * call returns XFLAT_ERR_TIMEOUT with the context intact.  0 restores normal operation. */
 int xflat_debug_barrier_extra(xflat_t h, uint32_t extra);
 
+/* Pass trace (profiling aid).  host_out == NULL: arm tracing of the first n_passes passes of every
+ * following step launch (n_passes = 0 disarms; the handle allocates n_passes x grid x 4 u64 of
+ * device memory).  host_out != NULL: synchronise and copy the trace out: for pass i and block b,
+ * host_out[(i*grid + b)*4 + 0..3] = %globaltimer (ns) at the pass start, after the block's beams and
+ * reduction, after the device-wide barrier let it go, and 1 if the block arrived last (then the
+ * third stamp is its arrival).  *grid_out (nullable) receives the number of blocks. */
+int xflat_debug_trace(xflat_t h, uint32_t n_passes, uint64_t* host_out, uint32_t* grid_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,7 @@ const double kSqrt2GFhc2 = std::sqrt(2.0) * kGF * kHbarcGevKm * kHbarcGevKm;
 
 constexpr uint32_t kMaxJJ = 128;          // combined angle bins per piece (shared-memory table rows)
 constexpr uint32_t kAlignBeams = 4;       // instance offsets and piece starts: 16-byte vectors
+uint32_t max_jj_cap(int nf, size_t real_size);
 
 struct HostInst {
   xflat_config cfg;
@@ -79,6 +80,8 @@ struct xflat_s {
   uint32_t steps_per_launch = 64;
   uint64_t timeout_ns = 2000000000ull;
   uint32_t debug_extra = 0;
+  unsigned long long* d_trace = nullptr;   // pass trace (xflat_debug_trace)
+  uint32_t trace_passes = 0;
   bool moments_valid = false;
   bool advancing = false;                  // last call was an xflat_advance launch
   std::string err;
@@ -124,8 +127,8 @@ int check_config(const xflat_config& c, std::string& why) {
     why = "bad power-law matter parameters"; return XFLAT_ERR_INVAL;
   }
   if (c.matter_kind == XFLAT_MATTER_CONSTANT && !is_fin(c.lambda_const_kmi)) { why = "bad lambda_const"; return XFLAT_ERR_INVAL; }
-  if (c.block_size != 0 && c.block_size != 128 && c.block_size != 256 && c.block_size != 512) {
-    why = "block_size must be 0, 128, 256 or 512"; return XFLAT_ERR_INVAL;
+  if (c.block_size != 0 && c.block_size != 128 && c.block_size != 256) {
+    why = "block_size must be 0, 128 or 256"; return XFLAT_ERR_INVAL;
   }
   return XFLAT_OK;
 }
@@ -374,7 +377,7 @@ void build_pieces(xflat_t h, int G) {
       const uint64_t lo = std::max<uint64_t>(s0, I.off), hi = std::min<uint64_t>(s1, I.off + I.n_beams);
       if (lo >= hi) continue;
       const uint32_t ne = I.cfg.n_energy;
-      const uint64_t maxlen = std::max<uint64_t>(kAlignBeams, ((uint64_t)(kMaxJJ - 1) * ne) / kAlignBeams * kAlignBeams);
+      const uint64_t maxlen = std::max<uint64_t>(kAlignBeams, ((uint64_t)(max_jj_cap(h->nf, h->real_size) - 1) * ne) / kAlignBeams * kAlignBeams);
       for (uint64_t a = lo; a < hi; a += maxlen) {
         const uint64_t e = std::min<uint64_t>(hi, a + maxlen);
         Piece p{};
@@ -391,9 +394,14 @@ void build_pieces(xflat_t h, int G) {
   h->blk[G] = (int)h->pieces.size();
 }
 
-size_t smem_bytes(size_t real_size, int max_jj) {
+// Values per (stage, angle bin) table row of the step kernel (Phys2<float>::KT, Phys2<double>::KT,
+// Phys3::KT), and the cap on angle bins per piece that bounds the table's shared memory.
+int table_row_values(int nf, size_t real_size) { return nf == 2 ? (real_size == 4 ? 24 : 8) : 4; }
+uint32_t max_jj_cap(int nf, size_t real_size) { return (nf == 2 && real_size == 4) ? 64u : kMaxJJ; }
+
+size_t smem_bytes(int nf, size_t real_size, int max_jj) {
   size_t s = 32 * kNMMax * sizeof(double);
-  s += (size_t)kMaxStages * max_jj * 2 * real_size;
+  s += (size_t)kMaxStages * max_jj * table_row_values(nf, real_size) * real_size;
   s += (size_t)max_jj * real_size;
   return (s + 15) / 16 * 16;
 }
@@ -423,6 +431,8 @@ KParams make_params(xflat_t h, int n_steps, int init_only) {
   p.init_only = init_only;
   p.max_jj = h->max_jj;
   p.integrator = h->integrator;
+  p.trace = init_only ? nullptr : h->d_trace;
+  p.trace_passes = (int)h->trace_passes;
   return p;
 }
 
@@ -451,7 +461,7 @@ int clear_sync_words(xflat_t h) {
   CUDA_TRY(h, cudaMemsetAsync(h->d_words, 0, 2 * sizeof(int), h->stream));
   CUDA_TRY(h, cudaMemsetAsync(h->d_nonfinite, 0, h->inst.size() * sizeof(int), h->stream));
   CUDA_TRY(h, cudaMemsetAsync(h->d_errmax, 0, h->inst.size() * sizeof(unsigned long long), h->stream));
-  CUDA_TRY(h, cudaMemsetAsync(h->d_acc, 0, h->inst.size() * kMaxStages * kNMMax * 2 * sizeof(unsigned long long), h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_acc, 0, h->inst.size() * kAccWordsPerInst * sizeof(unsigned long long), h->stream));
   return XFLAT_OK;
 }
 
@@ -494,10 +504,14 @@ int refresh_moments(xflat_t h) {
 }
 
 int setup_launch_shape(xflat_t h, const xflat_config& c) {
-  h->kernel = step_kernel_ptr(h->nf, h->precision, h->integrator);
-  if (!h->kernel) return fail(h, XFLAT_ERR_UNSUPPORTED, "no kernel for this flavour/precision/integrator");
+  // mixed two-flavour kernels exist at two register budgets: 768 resident threads per SM (80
+  // registers) and 512 (128 registers); the request picks the one that fits.  Every other kernel
+  // is built for one 256-thread block per SM.  Default: 256 threads x 3 blocks.
   h->block = c.block_size ? (int)c.block_size : 256;
-  const size_t smax = smem_bytes(h->real_size, kMaxJJ);
+  const int want_bps = c.blocks_per_sm ? (int)c.blocks_per_sm : (768 / h->block);
+  h->kernel = step_kernel_ptr(h->nf, h->precision, h->integrator, want_bps * h->block >= 768 ? 3 : 2);
+  if (!h->kernel) return fail(h, XFLAT_ERR_UNSUPPORTED, "no kernel for this flavour/precision/integrator");
+  const size_t smax = smem_bytes(h->nf, h->real_size, max_jj_cap(h->nf, h->real_size));
   CUDA_TRY(h, cudaFuncSetAttribute(h->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
   int occ = 0;
   CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h->kernel, h->block, smax));
@@ -511,7 +525,7 @@ int setup_launch_shape(xflat_t h, const xflat_config& c) {
   G = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)G, (T + per_block - 1) / per_block));
   h->grid = G;
   build_pieces(h, G);
-  h->smem = smem_bytes(h->real_size, h->max_jj);
+  h->smem = smem_bytes(h->nf, h->real_size, h->max_jj);
   CUDA_TRY(h, cudaMalloc(&h->d_pieces, sizeof(Piece) * std::max<size_t>(1, h->pieces.size())));
   CUDA_TRY(h, cudaMalloc(&h->d_blk, sizeof(int) * h->blk.size()));
   CUDA_TRY(h, cudaMemcpy(h->d_pieces, h->pieces.data(), sizeof(Piece) * h->pieces.size(), cudaMemcpyHostToDevice));
@@ -660,7 +674,7 @@ int create_impl(const xflat_config* cfgs, uint32_t n, xflat_t* out) {
   if (cudaMalloc(&h->planes, plane_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
   if (cudaMalloc(&h->d_ic, sizeof(InstConst) * n) != cudaSuccess ||
       cudaMalloc(&h->d_dyn, sizeof(InstDyn) * n) != cudaSuccess ||
-      cudaMalloc(&h->d_acc, sizeof(unsigned long long) * n * kMaxStages * kNMMax * 2) != cudaSuccess ||
+      cudaMalloc(&h->d_acc, sizeof(unsigned long long) * n * kAccWordsPerInst) != cudaSuccess ||
       cudaMalloc(&h->d_errmax, sizeof(unsigned long long) * n) != cudaSuccess ||
       cudaMalloc(&h->d_nonfinite, sizeof(int) * n) != cudaSuccess ||
       cudaMalloc(&h->d_etab, (size_t)eoff * h->real_size) != cudaSuccess ||
@@ -733,7 +747,8 @@ int xflat_destroy(xflat_t h) {
   if (!h) return XFLAT_OK;
   if (h->stream || true) cudaStreamSynchronize(h->stream);
   void* ptrs[] = {h->planes, h->d_ic, h->d_dyn, h->d_pieces, h->d_blk, h->d_acc, h->d_errmax,
-                  h->d_nonfinite, h->d_etab, h->d_u, h->d_du, h->d_bar, h->d_words, h->d_stage};
+                  h->d_nonfinite, h->d_etab, h->d_u, h->d_du, h->d_bar, h->d_words, h->d_stage,
+                  h->d_trace};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->h_words) cudaFreeHost(h->h_words);
@@ -839,8 +854,11 @@ int xflat_moments_inst(xflat_t h, uint32_t inst, double* J0, double* J1) {
   const InstDyn& d = h->dyn[inst];
   const double ws = h->ic[inst].wscale;
   const int nf = h->nf;
+  const int ncomp = nf == 2 ? 3 : 9;
   for (int t = 0; t < 2; ++t) {
-    const double* m = d.mom[1] + t * (nf == 2 ? 3 : 9);
+    // the device reduces D = J0 - J1 (slots 0..ncomp-1) and J1 (slots ncomp..2 ncomp-1)
+    double m[9];
+    for (int c = 0; c < ncomp; ++c) m[c] = d.mom[1][ncomp + c] + (t == 0 ? d.mom[1][c] : 0.0);
     double* J = t == 0 ? J0 : J1;
     std::memset(J, 0, sizeof(double) * 2 * nf * nf);
     if (nf == 2) {
@@ -1010,6 +1028,29 @@ const char* xflat_last_error(xflat_t h) { return h ? h->err.c_str() : "NULL hand
 int xflat_debug_barrier_extra(xflat_t h, uint32_t extra) {
   if (!h) return XFLAT_ERR_INVAL;
   h->debug_extra = extra;
+  return XFLAT_OK;
+}
+
+int xflat_debug_trace(xflat_t h, uint32_t n_passes, uint64_t* host_out, uint32_t* grid_out) {
+  if (!h) return XFLAT_ERR_INVAL;
+  if (grid_out) *grid_out = (uint32_t)h->grid;
+  if (host_out) {
+    if (!h->d_trace) return fail(h, XFLAT_ERR_STATE, "trace not armed");
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    CUDA_TRY(h, cudaMemcpy(host_out, h->d_trace, (size_t)h->trace_passes * h->grid * 4 * 8, cudaMemcpyDeviceToHost));
+    return XFLAT_OK;
+  }
+  if (h->d_trace) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_trace);
+    h->d_trace = nullptr;
+    h->trace_passes = 0;
+  }
+  if (n_passes == 0) return XFLAT_OK;
+  const size_t bytes = (size_t)n_passes * h->grid * 4 * 8;
+  CUDA_TRY(h, cudaMalloc(&h->d_trace, bytes));
+  CUDA_TRY(h, cudaMemset(h->d_trace, 0, bytes));
+  h->trace_passes = n_passes;
   return XFLAT_OK;
 }
 

@@ -56,6 +56,23 @@ __global__ void barrier_k(unsigned* count, volatile unsigned* gen, int nb, unsig
     __syncthreads();
   }
 }
+// Latency of dependent FP64 operations in one thread (clock64 cycles per operation).
+__global__ void lat64(double* out, long long* cyc, int n, double x0){
+  double x = x0, y = 1.000001;
+  long long t0 = clock64();
+  for(int i=0;i<n;i++) x = fma(x, y, 1e-9);
+  long long t1 = clock64();
+  for(int i=0;i<n;i++) x = 1.0 / (x + 1.5);
+  long long t2 = clock64();
+  for(int i=0;i<n;i++) x = sqrt(x + 2.0);
+  long long t3 = clock64();
+  for(int i=0;i<n;i++) x = pow(x + 1.1, -0.2);
+  long long t4 = clock64();
+  float f = (float)x;
+  for(int i=0;i<n;i++) f = fmaf(f, 1.000001f, 1e-9f);
+  long long t5 = clock64();
+  out[0] = x + f; cyc[0] = t1-t0; cyc[1] = t2-t1; cyc[2] = t3-t2; cyc[3] = t4-t3; cyc[4] = t5-t4;
+}
 int main(){
   cudaDeviceProp p; CK(cudaGetDeviceProperties(&p,0));
   printf("name %s SMs %d L2 %d MB smemPerBlockOptin %zu regsPerSM %d\n", p.name, p.multiProcessorCount, p.l2CacheSize>>20, p.sharedMemPerBlockOptin, p.regsPerMultiprocessor);
@@ -83,6 +100,15 @@ int main(){
     cudaEventRecord(a); CK(cudaLaunchCooperativeKernel((void*)barrier_k, G, 256, args, 0, 0)); cudaEventRecord(b); CK(cudaEventSynchronize(b)); cudaEventElapsedTime(&ms,a,b);
     unsigned long long he; cudaMemcpy(&he,err,8,cudaMemcpyDeviceToHost);
     printf("grid barrier G=%d: %.3f us/barrier (timeouts %llu)\n", G, ms*1e3/nb, he);
+  }
+  {
+    double* od; long long* cy; CK(cudaMalloc(&od, 64)); CK(cudaMalloc(&cy, 64));
+    for (int rep = 0; rep < 2; ++rep) {
+      lat64<<<1,1>>>(od, cy, 256, 0.5); CK(cudaDeviceSynchronize());
+      long long hc[5]; cudaMemcpy(hc, cy, sizeof(hc), cudaMemcpyDeviceToHost);
+      if (rep) printf("dependent-op latency (cycles/op): dfma %.1f ddiv %.1f dsqrt %.1f pow %.1f ffma %.1f\n",
+                      hc[0]/256.0, hc[1]/256.0, hc[2]/256.0, hc[3]/256.0, hc[4]/256.0);
+    }
   }
   size_t N=1ull<<28; float *x,*y; CK(cudaMalloc(&x,N*4)); CK(cudaMalloc(&y,N*4)); CK(cudaMemset(x,0,N*4));
   for(int r=0;r<3;r++){ cudaEventRecord(a); cudaMemcpyAsync(y,x,N*4,cudaMemcpyDeviceToDevice); cudaEventRecord(b); CK(cudaEventSynchronize(b)); cudaEventElapsedTime(&ms,a,b);

@@ -2,7 +2,7 @@
 //
 // One cooperative launch advances every active instance by up to n_steps radial steps.  A step is a
 // sequence of passes over all beams separated by device-wide barriers, because every stage of the
-// integrator needs the two angular moments of *all* beams (Eq. Hnu / Eq. F):
+// integrator needs the angular moments of *all* beams (Eq. Hnu / Eq. F):
 //
 //   pass p (p = 0 .. S-2): rebuild the stage state Y_{p+2} of every beam from the step's initial
 //       state y and the stage constants of the earlier stages (the stage derivatives k_1..k_{p+1}
@@ -12,14 +12,25 @@
 //       step) or the error norm (DP45).
 //
 // So every pass reads each beam's state once (128-bit vector loads of the SoA planes) and a step
-// writes it once: the algorithmic traffic of a streaming stage update.
+// writes it once.
 //
-// Moments.  Each thread accumulates its beams' contributions (working precision), each block
-// reduces them with a fixed shuffle/shared-memory tree in double, and each block adds its double
-// partial to the instance accumulator as a 128-bit fixed-point integer.  Integer addition is
-// associative, so the grid-level sum is exact to 2^-64 and identical whatever order the blocks
-// arrive in.  The last block to arrive at the barrier converts the accumulators, derives the stage
-// constants mu(r_s) j0, mu(r_s) j1, lambda(r_s) and runs the step-size controller in double.
+// Moments without cancellation.  With the measure of Eq. Hnu in u-bins, the nu-nu term of beam b is
+// mu(r) (J0 - cos(th_b) J1), J0 = sum w s / cos(th), J1 = sum w s.  Far from the neutrino sphere
+// J0 and J1 agree to O(R^2/r^2) and the difference cancels catastrophically in FP32.  The kernel
+// therefore reduces J1 and D = J0 - J1 = sum w s (1/cos(th) - 1), and assembles
+// J0 - cos(th_b) J1 = D + (1 - cos(th_b)) J1, with 1 - cos = u x / (1 + cos), x = R^2/r^2, and
+// 1/cos - 1 = (1 - cos)/cos: every term is computed without cancellation.
+//
+// Reduction.  Each thread accumulates its beams' contributions in the working precision.  FP64
+// path: each block reduces them with a fixed shuffle/shared-memory tree in double and adds its
+// partial to the instance accumulator as a 128-bit fixed-point integer (exact to 2^-64).  Mixed
+// path: each warp reduces with a fixed FP32 shuffle tree and its lane 0 adds the warp's partial as a
+// fixed-point integer with 48 fractional bits, converted from the float's bits on the integer pipe
+// (GB300's FP64 pipe is ~1/68 of its FP32 rate, so a double tree per block would cost more than the
+// beams themselves).  Integer addition is associative, so either grid-level sum is identical
+// whatever order the blocks arrive in.  The last block to arrive at the barrier converts the
+// accumulators, derives the stage constants mu(r_s) D, mu(r_s) J1, lambda(r_s) and runs the
+// step-size controller in double.
 #pragma once
 
 #include "xflat_internal.cuh"
@@ -78,6 +89,9 @@ struct TabCF4 {
   static constexpr int S = 4;
   static constexpr int kPasses = 4;
   static constexpr bool kAdaptive = false;
+  __host__ __device__ static constexpr double a(int, int) { return 0.0; }
+  __host__ __device__ static constexpr double b(int) { return 0.0; }
+  __host__ __device__ static constexpr double e(int) { return 0.0; }
   __host__ __device__ static constexpr double c(int i) { return TabRK4::c(i); }
 };
 
@@ -85,43 +99,106 @@ struct TabCF4 {
 template <typename Real>
 __host__ __device__ constexpr Real rbig() { return sizeof(Real) == 4 ? Real(3.0e38) : Real(1.7e308); }
 
+// Geometry of one (stage radius, angle bin): cos, 1/cos, 1 - cos, 1/cos - 1 without cancellation.
+struct Geo { double q, t1, t2; };
+__device__ __forceinline__ Geo geometry(double u, double x) {
+  const double c = sqrt(fma(-u, x, 1.0));
+  const double t2 = u * x / (1.0 + c);          // 1 - cos
+  const double q = 1.0 / c;                     // 1 / cos
+  return {q, t2 * q, t2};                       // t1 = 1/cos - 1 = (1 - cos)/cos
+}
+__device__ __forceinline__ void geometry_f(double u, double x, float& q, float& t1, float& t2) {
+  const float om = (float)fma(-u, x, 1.0);      // 1 - u x in double (no cancellation), then FP32
+  const float ux = (float)(u * x);
+  const float c = sqrtf(om);
+  q = 1.0f / c;
+  t2 = ux / (1.0f + c);
+  t1 = t2 * q;
+}
+
 // --------------------------------------------------------------------------------------------
 // Physics policies.  "Real" is the working precision of the per-beam algebra.
 //
 // Two flavours: the state of a beam is the Bloch vector s of P = (1 + s.sigma)/2 (antineutrinos:
-// of conj(Pbar), so that every beam obeys ds/dr = K x s with
-//   K = [eta omega_k B + lambda(r) z + mu(r) (j0 - cos(th) j1)] / cos(th),
-// eta = +1 / -1 for nu / nubar, B = (sin 2 theta_v, 0, -cos 2 theta_v)), which is
+// of conj(Pbar)), and every beam obeys ds/dr = K x s with
+//   K = [eta omega_k B + lambda(r) z + mu(r) (D + (1 - cos th) J1)] / cos th,
+// eta = +1 / -1 for nu / nubar, B = (sin 2 theta_v, 0, -cos 2 theta_v): this is
 // d(rho)/dr = -i [H, rho] / cos(th) of Eq. eom with H = (1/2) h.sigma.
+//
+// Per (stage, angle bin) table row: t1 = 1/cos - 1, q = 1/cos, q Bx, q Bz, G0x, G0y, G0z with
+// G0 = q (lambda z + mu D + (1 - cos) mu J1), so that K = eta omega (q Bx, 0, q Bz) + G0, followed
+// (FP32 only) by the negated q Bx, q Bz, G0.  FP64 rows hold the 7 values (KT = 8).  FP32 rows hold
+// 12 values each stored twice (KT = 24): a 64-bit load then yields a packed f32x2 operand for the
+// two beams a thread processes together (both share the angle bin), see PairRK.
 template <typename Real>
 struct Phys2 {
-  static constexpr int NC = 3, NM = kNM2, NSC = kNSC2;
-  struct Consts { Real B[3]; };
-  struct Beam { Real eo; Real w; };   // eta*omega_k, signed weight du_j * g_{sigma,k}
+  static constexpr bool kF32 = sizeof(Real) == 4;
+  static constexpr int NC = 3, NM = kNM2, NSC = kNSC2, KT = kF32 ? 24 : 8;
+  enum : int { vT1 = 0, vQ = 1, vQBX = 2, vQBZ = 3, vG0X = 4, vG0Y = 5, vG0Z = 6,
+               vNQBX = 7, vNQBZ = 8, vNG0X = 9, vNG0Y = 10, vNG0Z = 11 };
+  struct Consts { double B[3]; };
+  struct Beam { Real eo; Real w; };   // eta * omega_k, signed weight du_j * g_{sigma,k}
 
-  // stage constant block (Real): m0[3], m1[3], lam
-  __device__ static inline void K(const Consts& C, const Beam& bm, const Real* sc, Real q, Real c,
+  __device__ static inline Real val(const Real* t, int v) { return kF32 ? t[2 * v] : t[v]; }
+  __device__ static inline void put(Real* t, int v, Real x) {
+    if (kF32) { t[2 * v] = x; t[2 * v + 1] = x; } else { t[v] = x; }
+  }
+  __device__ static inline Real t1(const Real* t) { return val(t, vT1); }
+
+  // sc: mu D (3), mu J1 (3), lambda
+  __device__ static inline void fill(Real* t, const Geo& g, const double* sc, const Consts& C) {
+    put(t, vT1, (Real)g.t1);
+    put(t, vQ, (Real)g.q);
+    put(t, vQBX, (Real)(g.q * C.B[0]));
+    put(t, vQBZ, (Real)(g.q * C.B[2]));
+    put(t, vG0X, (Real)(g.q * (sc[0] + g.t2 * sc[3])));
+    put(t, vG0Y, (Real)(g.q * (sc[1] + g.t2 * sc[4])));
+    put(t, vG0Z, (Real)(g.q * (sc[6] + sc[2] + g.t2 * sc[5])));
+    if (!kF32) t[7] = 0;
+  }
+  __device__ static inline void fill_f(Real* t, float q, float t1v, float t2, const float* scf,
+                                       const Consts& C) {
+    const float qbx = q * (float)C.B[0], qbz = q * (float)C.B[2];
+    const float gx = q * (scf[0] + t2 * scf[3]);
+    const float gy = q * (scf[1] + t2 * scf[4]);
+    const float gz = q * (scf[6] + scf[2] + t2 * scf[5]);
+    put(t, vT1, t1v);
+    put(t, vQ, q);
+    put(t, vQBX, qbx);
+    put(t, vQBZ, qbz);
+    put(t, vG0X, gx);
+    put(t, vG0Y, gy);
+    put(t, vG0Z, gz);
+    if (kF32) {
+      put(t, vNQBX, -qbx);
+      put(t, vNQBZ, -qbz);
+      put(t, vNG0X, -gx);
+      put(t, vNG0Y, -gy);
+      put(t, vNG0Z, -gz);
+    }
+  }
+  __device__ static inline void K(const Real* t, const Beam& bm, const Real*, const Real*,
                                   Real (&Kv)[3]) {
-    Kv[0] = (bm.eo * C.B[0] + sc[0]) * q - sc[3];
-    Kv[1] = sc[1] * q - sc[4];
-    Kv[2] = (bm.eo * C.B[2] + sc[6] + sc[2]) * q - sc[5];
+    Kv[0] = bm.eo * val(t, vQBX) + val(t, vG0X);
+    Kv[1] = val(t, vG0Y);
+    Kv[2] = bm.eo * val(t, vQBZ) + val(t, vG0Z);
   }
   __device__ static inline void f(const Real (&Kv)[3], const Real (&y)[3], Real (&k)[3]) {
     k[0] = Kv[1] * y[2] - Kv[2] * y[1];
     k[1] = Kv[2] * y[0] - Kv[0] * y[2];
     k[2] = Kv[0] * y[1] - Kv[1] * y[0];
   }
-  __device__ static inline void accum(Real (&acc)[NM], Real w, Real q, const Real (&y)[3]) {
-    const Real wq = w * q;
+  // moments D (weight w t1) and J1 (weight w)
+  __device__ static inline void accum(Real (&acc)[NM], Real w, Real t1, const Real (&y)[3]) {
+    const Real wt = w * t1;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { acc[i] += wq * y[i]; acc[3 + i] += w * y[i]; }
+    for (int i = 0; i < 3; ++i) { acc[i] += wt * y[i]; acc[3 + i] += w * y[i]; }
   }
   // Frobenius norm^2 of the traceless part of P = (1 + s.sigma)/2: |s|^2 / 2
   __device__ static inline Real tnorm2(const Real (&y)[3]) {
     return Real(0.5) * (y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
   }
-  // Frobenius norm of a traceless matrix e = (e.sigma)/2 given by its Bloch vector, computed with a
-  // scale so that it cannot overflow; +inf if a component is not finite
+  // Frobenius norm of the traceless matrix (e.sigma)/2, scaled so it cannot overflow; +inf if not finite
   __device__ static inline Real enorm(const Real (&e)[3]) {
     const Real m = fmax(fabs(e[0]), fmax(fabs(e[1]), fabs(e[2])));
     if (!(m <= rbig<Real>())) return Real(INFINITY);
@@ -140,37 +217,49 @@ struct Phys2 {
 
 // Three flavours: the state is the full 3x3 Hermitian density matrix (9 reals: P00, P11, P22,
 // Re P01, Im P01, Re P02, Im P02, Re P12, Im P12) of P (nu) or conj(Pbar) (nubar); the derivative
-// is -i [K, P] with the Hermitian K = [eta (omega21 M21 + omega31 M31) + lambda E_ee + mu (J0 - cos J1)]
-// / cos(th), M21/M31 the real unit vacuum matrices U diag(0,1,0) U^T and U diag(0,0,1) U^T.
+// is -i [K, P] with the Hermitian
+//   K = [eta (omega21 M21 + omega31 M31) + lambda E_ee + mu (D + (1 - cos) J1)] / cos,
+// M21/M31 the real unit vacuum matrices U diag(0,1,0) U^T and U diag(0,0,1) U^T.
+// Table row (KT = 4): q, t1, t2, pad; the stage constants mu D, mu J1, lambda stay per stage.
 template <typename Real>
 struct Phys3 {
-  static constexpr int NC = 9, NM = kNM3, NSC = kNSC3;
-  struct Consts { Real M21[6], M31[6]; };
+  static constexpr int NC = 9, NM = kNM3, NSC = kNSC3, KT = 4;
+  struct Consts { double M21[6], M31[6]; };
   struct Beam { Real o21, o31; Real w; };
 
-  // stage constants: m0[9], m1[9], lam
-  __device__ static inline void K(const Consts& C, const Beam& bm, const Real* sc, Real q, Real c,
+  __device__ static inline Real t1(const Real* t) { return t[1]; }
+  __device__ static inline void fill(Real* t, const Geo& g, const double*, const Consts&) {
+    t[0] = (Real)g.q;
+    t[1] = (Real)g.t1;
+    t[2] = (Real)g.t2;
+    t[3] = 0;
+  }
+  __device__ static inline void fill_f(Real* t, float q, float t1, float t2, const float*, const Consts&) {
+    t[0] = q;
+    t[1] = t1;
+    t[2] = t2;
+    t[3] = 0;
+  }
+  // vac: the six real entries (00,11,22,01,02,12) of M21, M31 in working precision;
+  // sc (working precision): mu D (9), mu J1 (9), lambda
+  __device__ static inline void K(const Real* t, const Beam& bm, const Real* vac, const Real* sc,
                                   Real (&Kv)[9]) {
-    // vacuum part (real symmetric): order 00,11,22,01,02,12
-    const Real v00 = bm.o21 * C.M21[0] + bm.o31 * C.M31[0];
-    const Real v11 = bm.o21 * C.M21[1] + bm.o31 * C.M31[1];
-    const Real v22 = bm.o21 * C.M21[2] + bm.o31 * C.M31[2];
-    const Real v01 = bm.o21 * C.M21[3] + bm.o31 * C.M31[3];
-    const Real v02 = bm.o21 * C.M21[4] + bm.o31 * C.M31[4];
-    const Real v12 = bm.o21 * C.M21[5] + bm.o31 * C.M31[5];
-    Kv[0] = (v00 + sc[18] + sc[0]) * q - sc[9];
-    Kv[1] = (v11 + sc[1]) * q - sc[10];
-    Kv[2] = (v22 + sc[2]) * q - sc[11];
-    Kv[3] = (v01 + sc[3]) * q - sc[12];
-    Kv[4] = sc[4] * q - sc[13];
-    Kv[5] = (v02 + sc[5]) * q - sc[14];
-    Kv[6] = sc[6] * q - sc[15];
-    Kv[7] = (v12 + sc[7]) * q - sc[16];
-    Kv[8] = sc[8] * q - sc[17];
+    const Real q = t[0], t2 = t[2];
+    Real v[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = bm.o21 * vac[i] + bm.o31 * vac[6 + i];
+    Kv[0] = q * (v[0] + sc[18] + sc[0] + t2 * sc[9]);
+    Kv[1] = q * (v[1] + sc[1] + t2 * sc[10]);
+    Kv[2] = q * (v[2] + sc[2] + t2 * sc[11]);
+    Kv[3] = q * (v[3] + sc[3] + t2 * sc[12]);
+    Kv[4] = q * (sc[4] + t2 * sc[13]);
+    Kv[5] = q * (v[4] + sc[5] + t2 * sc[14]);
+    Kv[6] = q * (sc[6] + t2 * sc[15]);
+    Kv[7] = q * (v[5] + sc[7] + t2 * sc[16]);
+    Kv[8] = q * (sc[8] + t2 * sc[17]);
   }
   // Z = -i [K, Y] for Hermitian K, Y; A = K Y, Z_aa = 2 Im A_aa, Z_ab = -i (A_ab - conj(A_ba)).
   __device__ static inline void f(const Real (&Kv)[9], const Real (&y)[9], Real (&z)[9]) {
-    // complex entries: K_ab = kr[a][b] + i ki[a][b]
     const Real kr[3][3] = {{Kv[0], Kv[3], Kv[5]}, {Kv[3], Kv[1], Kv[7]}, {Kv[5], Kv[7], Kv[2]}};
     const Real ki[3][3] = {{0, Kv[4], Kv[6]}, {-Kv[4], 0, Kv[8]}, {-Kv[6], -Kv[8], 0}};
     const Real yr[3][3] = {{y[0], y[3], y[5]}, {y[3], y[1], y[7]}, {y[5], y[7], y[2]}};
@@ -192,7 +281,6 @@ struct Phys3 {
     z[0] = 2 * ai[0][0];
     z[1] = 2 * ai[1][1];
     z[2] = 2 * ai[2][2];
-    // Z_ab = -i (A_ab - conj(A_ba)) = (ai_ab + ai_ba) + i (-(ar_ab - ar_ba))
     z[3] = ai[0][1] + ai[1][0];
     z[4] = ar[1][0] - ar[0][1];
     z[5] = ai[0][2] + ai[2][0];
@@ -200,10 +288,10 @@ struct Phys3 {
     z[7] = ai[1][2] + ai[2][1];
     z[8] = ar[2][1] - ar[1][2];
   }
-  __device__ static inline void accum(Real (&acc)[NM], Real w, Real q, const Real (&y)[9]) {
-    const Real wq = w * q;
+  __device__ static inline void accum(Real (&acc)[NM], Real w, Real t1, const Real (&y)[9]) {
+    const Real wt = w * t1;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) { acc[i] += wq * y[i]; acc[9 + i] += w * y[i]; }
+    for (int i = 0; i < 9; ++i) { acc[i] += wt * y[i]; acc[9 + i] += w * y[i]; }
   }
   // ||P - tr(P)/3||_F^2 with off-diagonal entries counted twice
   __device__ static inline Real tnorm2(const Real (&y)[9]) {
@@ -255,6 +343,10 @@ struct KParams {
   int init_only;
   int max_jj;
   int integrator;
+  // optional pass trace (NULL: off): per pass and block, %globaltimer at pass start, after the
+  // block's beams and reduction, after the barrier released it, and 1 if it was the last block
+  unsigned long long* trace;
+  int trace_passes;
 };
 
 __device__ __forceinline__ void fx_add(unsigned long long* acc2, double x) {
@@ -269,126 +361,240 @@ __device__ __forceinline__ void fx_add(unsigned long long* acc2, double x) {
 
 __device__ __forceinline__ double fx_read(const unsigned long long* acc2) {
   const long long hi = (long long)acc2[1];
-  return (double)hi + (double)acc2[0] * 5.421010862427522e-20;   // 2^-64
+  return (double)hi + (double)acc2[0] * 5.421010862427522e-20;   // 2^-64 (words already loaded)
+}
+
+// Mixed precision: a float as a signed fixed-point integer with 48 fractional bits, from its bits
+// alone (integer pipe only; |v| < 2^14 required, truncated toward zero below 2^-48).  Returns
+// false when |v| is too large or not finite.
+__device__ __forceinline__ bool f32_to_fix48(float v, long long& out) {
+  const unsigned int b = __float_as_uint(v);
+  const int e = (int)((b >> 23) & 0xffu);
+  if (e == 0xff || e >= 127 + 14) return false;
+  if (e == 0) { out = 0; return true; }                  // zero or below 2^-126
+  const long long m = (long long)((b & 0x7fffffu) | 0x800000u);   // value = m 2^(e-150)
+  const int sh = e - 102;                                // x 2^48
+  long long f = sh >= 0 ? (m << sh) : (sh > -25 ? (m >> (-sh)) : 0ll);
+  out = (b >> 31) ? -f : f;
+  return true;
+}
+
+// Accumulator read-out: 128-bit (FP64 path) or 48-bit-fraction (mixed path) fixed point.
+template <typename Real>
+__device__ __forceinline__ double acc_read(const unsigned long long* acc2) {
+  if constexpr (sizeof(Real) == 4) return (double)(long long)acc2[0] * 3.552713678800501e-15;  // 2^-48
+  else return fx_read(acc2);
 }
 
 template <class Tab>
 __device__ __forceinline__ double stage_c(int i) { return Tab::c(i); }
 
-// Per-block shared state for the piece being processed.
-template <typename Real, int NSC>
-struct PieceShared {
-  Real sc[kMaxStages][NSC];      // stage constants in working precision
-  Real hA[kMaxStages][kMaxStages];
-  Real hB[kMaxStages];
-  Real hE[kMaxStages];
-  Real cB[3];                    // unused for 3 flavours
-  int inst;
-  int active;
-};
-
 // ------------------------------------------------------------------------------------------
 // The last block to arrive: reduce accumulators, derive stage constants, run the controller.
-template <class Phys, class Tab>
-__device__ void serial_update(const KParams& p, int slot, bool final_pass, bool init) {
+// Every value another block may have written since this SM last looked is read through L2
+// (__ldcg), never from a possibly stale L1 line; the loads are issued before any branch on them.
+// 0.9 Err^(-1/5), the unclamped step-size factor, in double.  The caller clamps it to [0.2, 5],
+// which decides alone below Err = (0.9/5)^5 = 1.8896e-4 and above (0.9/0.2)^5 = 1845.3, so only
+// (a slightly wider) range is computed: a float seed refined by two Newton steps for y^-5 = Err,
+// y <- y (1.2 - 0.2 Err y^5), which need no division (one FP64 pow costs ~5800 cycles of latency
+// on this part, the two steps ~800) and converge to double accuracy.
+__device__ __forceinline__ double controller_factor(double err) {
+  if (!(err > 1.5e-4)) return 5.0;
+  if (!(err < 2000.0)) return 0.0;
+  double y = (double)powf((float)err, -0.2f);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double y2 = y * y;
+    const double y5 = y2 * y2 * y;
+    y = y * fma(-0.2 * err, y5, 1.2);
+  }
+  return 0.9 * y;
+}
+
+// mu(r) and lambda(r) at one radius (double).
+__device__ __forceinline__ void strengths(const InstConst& ic, double r, double& mu, double& lam) {
+  const double inv = 1.0 / r;
+  mu = ic.mu_coef * inv * inv;
+  lam = 0.0;
+  if (ic.matter == kMatterPower) {
+    const double x = ic.r_ref * inv;
+    lam = ic.lam_coef * (ic.power == 3.0 ? x * x * x : pow(x, ic.power));
+  } else if (ic.matter == kMatterConst) {
+    lam = ic.lam_const;
+  }
+}
+
+template <class Phys, class Tab, typename Real>
+__device__ int serial_update(const KParams& p, int slot, bool final_pass, bool init) {
   constexpr int NM = Phys::NM;
   constexpr int NCOMP = NM / 2;
+  int all_finished = 1;                            // over this thread's instances
   for (int i = threadIdx.x; i < p.n_inst; i += blockDim.x) {
     const InstConst& ic = p.ic[i];
     InstDyn& d = p.dyn[i];
-    if (d.done || d.status) continue;
-    unsigned long long* acc = p.acc + ((size_t)i * kMaxStages + slot) * kNMMax * 2;
-    if (p.nonfinite[i]) {
+    const unsigned long long* acc = p.acc + (size_t)i * kAccWordsPerInst + (size_t)slot * kAccCopies * kNMMax * 2;
+    const bool have_moments = !(final_pass && Tab::kAdaptive);
+    const bool adaptive_final = final_pass && Tab::kAdaptive;
+    // ---- every load first (no store may sit between them) -------------------------------
+    const int done = __ldcg(&d.done), status = __ldcg(&d.status), nonfin = __ldcg(&p.nonfinite[i]);
+    const unsigned long long eb = __ldcg(&p.errmax[i]);
+    double m[NM];
+    if (have_moments) {
+      // sum the accumulator copies as integers (exact), then convert
+#pragma unroll
+      for (int c = 0; c < NM; ++c) {
+        if constexpr (sizeof(Real) == 4) {
+          long long sum = 0;
+#pragma unroll
+          for (int cp = 0; cp < kAccCopies; ++cp) sum += (long long)__ldcg(acc + ((size_t)cp * kNMMax + c) * 2);
+          m[c] = (double)sum * 3.552713678800501e-15;        // 2^-48
+        } else {
+          unsigned __int128 sum = 0;
+#pragma unroll
+          for (int cp = 0; cp < kAccCopies; ++cp) {
+            const unsigned long long* w = acc + ((size_t)cp * kNMMax + c) * 2;
+            sum += ((unsigned __int128)__ldcg(w + 1) << 64) | (unsigned __int128)__ldcg(w);
+          }
+          m[c] = (double)(long long)(unsigned long long)(sum >> 64) +
+                 (double)(unsigned long long)sum * 5.421010862427522e-20;   // 2^-64
+        }
+      }
+    }
+    double m7[NM], sc7[Phys::NSC];
+    if (adaptive_final) {
+#pragma unroll
+      for (int c = 0; c < NM; ++c) m7[c] = __ldcg(&d.mom[Tab::S][c]);
+#pragma unroll
+      for (int c = 0; c < Phys::NSC; ++c) sc7[c] = __ldcg(&d.sc[Tab::S][c]);
+    }
+    const int gslot = slot == 0 ? Tab::S : slot;   // slot 0: new state's moments at r + h
+    double mu = __ldcg(&d.mus[gslot]), lam = __ldcg(&d.lams[gslot]);
+    double r = __ldcg(&d.r), hh = __ldcg(&d.h);
+    const double r_end = __ldcg(&d.r_end), r0f = __ldcg(&d.r0_fixed), hf = __ldcg(&d.h_fixed);
+    long long nfix = __ldcg(&d.n_fixed);
+    const long long nfix_tot = __ldcg(&d.n_fixed_total);
+    int last = __ldcg(&d.last), parity = __ldcg(&d.parity);
+    unsigned long long accepted = __ldcg(&d.accepted), rejected = __ldcg(&d.rejected);
+    unsigned long long evals = __ldcg(&d.stage_evals);
+    if (done || status) continue;
+    if (nonfin) {
       d.status = 5;  // XFLAT_ERR_NONFINITE
       atomicCAS(p.status, 0, 5);
       continue;
     }
-    const bool have_moments = !(final_pass && Tab::kAdaptive);
+    // ---- stage constants of the stage just reduced (the accumulators are cleared elsewhere) --
     if (have_moments) {
-      double m[NM];
-      for (int c = 0; c < NM; ++c) {
-        m[c] = fx_read(acc + 2 * c);
-        acc[2 * c] = 0ull;
-        acc[2 * c + 1] = 0ull;
-      }
-      const double r = d.rs[slot];
-      const double mu = ic.mu_coef / (r * r);
-      double lam = 0.0;
-      if (ic.matter == kMatterPower) lam = ic.lam_coef * pow(ic.r_ref / r, ic.power);
+      if (init) strengths(ic, __ldcg(&d.rs[slot]), mu, lam);   // the host set only rs[1], xs[1]
       for (int c = 0; c < NM; ++c) d.mom[slot][c] = m[c];
       for (int c = 0; c < NCOMP; ++c) {
         d.sc[slot][c] = mu * m[c];
         d.sc[slot][NCOMP + c] = mu * m[NCOMP + c];
       }
-      d.sc[slot][NM] = ic.matter == kMatterConst ? ic.lam_const : lam;
+      d.sc[slot][NM] = lam;
     }
-    if (!final_pass && !init) continue;
+    if (!final_pass && !init) {
+      all_finished = 0;
+      continue;
+    }
     // ---- step bookkeeping ---------------------------------------------------------------
+    bool fin = false, step_err = false;
     if (init) {
-      d.stage_evals += Tab::kAdaptive ? 1ull : 0ull;
+      evals += Tab::kAdaptive ? 1ull : 0ull;
     } else if (!Tab::kAdaptive) {
-      d.parity ^= 1;
-      d.accepted += 1;
-      d.stage_evals += 4;
-      d.n_fixed += 1;
-      d.r = (d.n_fixed >= d.n_fixed_total) ? d.r_end : d.r0_fixed + (double)d.n_fixed * d.h_fixed;
-      if (d.n_fixed >= d.n_fixed_total) d.done = 1;
+      parity ^= 1;
+      accepted += 1;
+      evals += 4;
+      nfix += 1;
+      fin = nfix >= nfix_tot;
+      r = fin ? r_end : r0f + (double)nfix * hf;
       // the final pass reduced the new state's moments at r + h (= stage S radius): stage 1 of
       // the next step
-      for (int c = 0; c < NM; ++c) d.mom[1][c] = d.mom[slot][c];
-      for (int c = 0; c < Phys::NSC; ++c) d.sc[1][c] = d.sc[slot][c];
+      for (int c = 0; c < NM; ++c) d.mom[1][c] = m[c];
+      for (int c = 0; c < NCOMP; ++c) {
+        d.sc[1][c] = mu * m[c];
+        d.sc[1][NCOMP + c] = mu * m[NCOMP + c];
+      }
+      d.sc[1][NM] = lam;
     } else {
-      const double err = __longlong_as_double((long long)p.errmax[i]);
+      const double err = __longlong_as_double((long long)eb);
       p.errmax[i] = 0ull;
       d.err = err;
-      d.stage_evals += 6;
+      evals += 6;
       const bool ok = err <= 1.0;
-      double fac;
+      const double q = controller_factor(err);
       if (ok) {
-        d.r = d.last ? d.r_end : d.r + d.h;
-        d.parity ^= 1;
-        d.accepted += 1;
-        for (int c = 0; c < NM; ++c) d.mom[1][c] = d.mom[7][c];
-        for (int c = 0; c < Phys::NSC; ++c) d.sc[1][c] = d.sc[7][c];
-        fac = err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2)));
-        if (d.last) d.done = 1;
+        r = last ? r_end : r + hh;
+        parity ^= 1;
+        accepted += 1;
+        for (int c = 0; c < NM; ++c) d.mom[1][c] = m7[c];
+        for (int c = 0; c < Phys::NSC; ++c) d.sc[1][c] = sc7[c];
+        fin = last != 0;
       } else {
-        d.rejected += 1;
-        fac = fmax(0.2, 0.9 * pow(err, -0.2));
+        rejected += 1;
       }
-      d.h = fmin(d.h * fac, ic.h_max);
-      if (!d.done && d.h < ic.h_min) {
+      const double fac = ok ? fmin(5.0, fmax(0.2, q)) : fmax(0.2, q);
+      hh = fmin(hh * fac, ic.h_max);
+      if (!fin && hh < ic.h_min) {
         d.status = 6;  // XFLAT_ERR_STEP
         atomicCAS(p.status, 0, 6);
-        continue;
+        step_err = true;
       }
     }
-    if (d.done) continue;
-    // ---- geometry of the next step ------------------------------------------------------
-    double h;
-    if (Tab::kAdaptive) {
-      d.last = (d.r + d.h >= d.r_end) ? 1 : 0;
-      if (d.last) d.h = d.r_end - d.r;
-      h = d.h;
-    } else {
-      h = d.h_fixed;
+    // ---- the next step's clipped step size; its stage geometry follows in serial_geometry ----
+    if (!fin && Tab::kAdaptive) {
+      last = (r + hh >= r_end) ? 1 : 0;
+      if (last) hh = r_end - r;
     }
-    for (int s = 1; s <= Tab::S; ++s) {
-      const double rs = (s == 1) ? d.r : __dadd_rn(d.r, __dmul_rn(stage_c<Tab>(s), h));
-      d.rs[s] = rs;
-      d.xs[s] = ic.R2 / (rs * rs);
-    }
+    d.geo_pending = (!fin && !step_err) ? 1 : 0;
+    d.r = r;
+    d.h = hh;
+    d.last = last;
+    d.parity = parity;
+    d.n_fixed = nfix;
+    d.accepted = accepted;
+    d.rejected = rejected;
+    d.stage_evals = evals;
+    if (fin) d.done = 1;
+    if (!fin && !step_err) all_finished = 0;
   }
+  if (threadIdx.x < p.n_inst) __threadfence();    // results visible before the barrier release
+  return all_finished;
 }
 
+// The next step's stage radii, R^2/r^2, mu and lambda, one (instance, stage) per thread of the last
+// block: FP64 divisions have a long latency on this part, so they run side by side, not in a chain.
+// Reads the r, h and geo_pending that serial_update wrote in this block before a __syncthreads.
+template <class Tab>
+__device__ void serial_geometry(const KParams& p) {
+  bool wrote = false;
+  for (int t = threadIdx.x; t < p.n_inst * Tab::S; t += blockDim.x) {
+    const int i = t / Tab::S, s = t % Tab::S + 1;
+    InstDyn& d = p.dyn[i];
+    if (!d.geo_pending) continue;
+    const InstConst& ic = p.ic[i];
+    const double r = d.r, h = Tab::kAdaptive ? d.h : d.h_fixed;
+    const double rs = (s == 1) ? r : __dadd_rn(r, __dmul_rn(stage_c<Tab>(s), h));
+    double mus, lams;
+    strengths(ic, rs, mus, lams);
+    d.rs[s] = rs;
+    d.xs[s] = ic.R2 / (rs * rs);
+    d.mus[s] = mus;
+    d.lams[s] = lams;
+    wrote = true;
+  }
+  if (wrote) __threadfence();
+}
 
 // ------------------------------------------------------------------------------------------
 // Loads that must not hit a stale L1 line: instance dynamics change across barriers.
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
 
+// Per-thread state vectors: two consecutive beams per load (float2 / double2), so the loaded and
+// the prefetched vectors fit the register budget; a warp still reads 256 or 512 contiguous bytes
+// per plane.
 template <typename Real> struct Vec16;
-template <> struct Vec16<float> { using T = float4; static constexpr int N = 4; };
+template <> struct Vec16<float> { using T = float2; static constexpr int N = 2; };
 template <> struct Vec16<double> { using T = double2; static constexpr int N = 2; };
 
 template <typename Real>
@@ -436,14 +642,36 @@ __device__ __forceinline__ void rotate(const Real (&Om)[3], Real (&y)[3]) {
   y[2] += a * c2 + b * d2;
 }
 
-// Shared-memory view of one piece.
+// Per-block shared state of the piece being processed.
 template <typename Real, class Phys>
-struct PieceView {
-  const Real* cq;       // [kMaxStages][n_jj][2]: cos(theta), 1/cos(theta) at each stage radius
-  const Real* dut;      // [n_jj] du_j
+struct BlockShared {
+  double scd[kMaxStages][Phys::NSC];   // stage constants (double)
+  double xs[kMaxStages];               // R^2 / r_s^2
+  unsigned long long hA2[kMaxStages][kMaxStages];   // packed (h a_ij, h a_ij) for the FP32 pair path
+  unsigned long long hB2[kMaxStages];
+  unsigned long long hE2[kMaxStages];
+  Real scr[kMaxStages][Phys::NSC];     // stage constants in working precision
+  Real hA[kMaxStages][kMaxStages];
+  Real hB[kMaxStages];
+  Real hE[kMaxStages];
+  Real vac[12];                        // three flavours: M21, M31 in working precision
+  Real rtol, atol;
+  double fx[kNMMax];
+  int active;
+  int parity;
+  int flag;
+  int pass_idx;                        // passes run by this block in this launch (pass trace)
+  unsigned int gen_seen;               // barrier generation this block arrived in
+};
+
+// Table view: row (stage s, combined angle index tj) holds Phys::KT values.
+template <typename Real, class Phys>
+struct TabView {
+  const Real* t;
   int n_jj;
-  __device__ __forceinline__ Real c(int s, int jj) const { return cq[(s * n_jj + jj) * 2]; }
-  __device__ __forceinline__ Real q(int s, int jj) const { return cq[(s * n_jj + jj) * 2 + 1]; }
+  __device__ __forceinline__ const Real* row(int s, int tj) const {
+    return t + ((size_t)s * n_jj + tj) * Phys::KT;
+  }
 };
 
 // What a pass does (compile time).
@@ -457,10 +685,11 @@ template <class Phys, class Tab, typename Real, int kPass, int kKind>
 struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
   static constexpr int NC = Phys::NC;
   // number of stage derivatives to rebuild before the stage state of this pass
-  static constexpr int kChain = kKind == kInitPass ? 0 : (kKind == kFinalPass ? Tab::S - (Tab::kAdaptive ? 1 : 0) : kPass + 1);
-  template <class PS>
-  __device__ static inline void beam(const PS& ps, const typename Phys::Consts& C, const typename Phys::Beam& bm,
-                                     const PieceView<Real, Phys>& pv, int jj, Real (&y)[NC],
+  static constexpr int kChain =
+      kKind == kInitPass ? 0 : (kKind == kFinalPass ? Tab::S - (Tab::kAdaptive ? 1 : 0) : kPass + 1);
+  template <class BS>
+  __device__ static inline void beam(const BS& bs, const typename Phys::Beam& bm,
+                                     const TabView<Real, Phys>& tv, int tj, Real (&y)[NC],
                                      Real (&acc)[Phys::NM], Real& emax, int& bad, bool mixed) {
     Real k[Tab::S + 1][NC];
 #pragma unroll
@@ -471,15 +700,15 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
         Real v = y[i];
 #pragma unroll
         for (int m = 1; m < l; ++m)
-          if (Tab::a(l, m) != 0.0) v += ps.hA[l][m] * k[m][i];
+          if (Tab::a(l, m) != 0.0) v += bs.hA[l][m] * k[m][i];
         Y[i] = v;
       }
       Real Kv[NC];
-      Phys::K(C, bm, ps.sc[l], pv.q(l, jj), pv.c(l, jj), Kv);
+      Phys::K(tv.row(l, tj), bm, bs.vac, bs.scr[l], Kv);
       Phys::f(Kv, Y, k[l]);
     }
     if (kKind == kInitPass) {
-      Phys::accum(acc, bm.w, pv.q(1, jj), y);
+      Phys::accum(acc, bm.w, Phys::t1(tv.row(1, tj)), y);
       return;
     }
     if (kKind == kStagePass) {
@@ -490,11 +719,11 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
         Real v = y[i];
 #pragma unroll
         for (int m = 1; m < I; ++m)
-          if (Tab::a(I, m) != 0.0) v += ps.hA[I][m] * k[m][i];
+          if (Tab::a(I, m) != 0.0) v += bs.hA[I][m] * k[m][i];
         Y[i] = v;
       }
       if (Tab::kAdaptive && I == Tab::S && mixed) Phys::normalise(Y);
-      Phys::accum(acc, bm.w, pv.q(I, jj), Y);
+      Phys::accum(acc, bm.w, Phys::t1(tv.row(I, tj)), Y);
       return;
     }
     // final pass
@@ -504,16 +733,15 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
       Real v = y[i];
 #pragma unroll
       for (int m = 1; m <= kChain; ++m)
-        if (Tab::b(m) != 0.0) v += ps.hB[m] * k[m][i];
+        if (Tab::b(m) != 0.0) v += bs.hB[m] * k[m][i];
       yn[i] = v;
     }
-    const Real yn2 = Phys::tnorm2(yn);
-    const bool ynok = yn2 <= rbig<Real>();
+    const bool ynok = Phys::tnorm2(yn) <= rbig<Real>();
     if (mixed && ynok) Phys::normalise(yn);
     if (Tab::kAdaptive) {
       if (!(Phys::tnorm2(y) <= rbig<Real>())) bad = 1;     // non-finite input state: fatal
       Real Kv[NC];
-      Phys::K(C, bm, ps.sc[Tab::S], pv.q(Tab::S, jj), pv.c(Tab::S, jj), Kv);
+      Phys::K(tv.row(Tab::S, tj), bm, bs.vac, bs.scr[Tab::S], Kv);
       Phys::f(Kv, yn, k[Tab::S]);
       Real e[NC];
 #pragma unroll
@@ -521,17 +749,17 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
         Real v = 0;
 #pragma unroll
         for (int m = 1; m <= Tab::S; ++m)
-          if (Tab::e(m) != 0.0) v += ps.hE[m] * k[m][i];
+          if (Tab::e(m) != 0.0) v += bs.hE[m] * k[m][i];
         e[i] = v;
       }
       const Real en = Phys::enorm(e);
       const Real sn = sqrt(fmax(Phys::tnorm2(y), Phys::tnorm2(yn)));
-      Real ratio = en / (ps.atol + ps.rtol * sn);
+      Real ratio = en / (bs.atol + bs.rtol * sn);
       // a trial step whose stages overflowed the working precision is rejected, not fatal
       if (!(ratio <= rbig<Real>()) || !ynok) ratio = Real(INFINITY);
       emax = fmax(emax, ratio);
     } else {
-      Phys::accum(acc, bm.w, pv.q(Tab::S, jj), yn);
+      Phys::accum(acc, bm.w, Phys::t1(tv.row(Tab::S, tj)), yn);
     }
 #pragma unroll
     for (int i = 0; i < NC; ++i) y[i] = yn[i];
@@ -542,33 +770,33 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
 template <class Phys, class Tab, typename Real, int kPass, int kKind>
 struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
   static constexpr int NC = 3;
-  template <class PS>
-  __device__ static inline void beam(const PS& ps, const typename Phys::Consts& C, const typename Phys::Beam& bm,
-                                     const PieceView<Real, Phys>& pv, int jj, Real (&y)[NC],
+  template <class BS>
+  __device__ static inline void beam(const BS& bs, const typename Phys::Beam& bm,
+                                     const TabView<Real, Phys>& tv, int tj, Real (&y)[NC],
                                      Real (&acc)[Phys::NM], Real& emax, int& bad, bool mixed) {
     if (kKind == kInitPass) {
-      Phys::accum(acc, bm.w, pv.q(1, jj), y);
+      Phys::accum(acc, bm.w, Phys::t1(tv.row(1, tj)), y);
       return;
     }
-    const Real h = ps.hB[0];
+    const Real h = bs.hB[0];
     Real K1[3], K2[3], K3[3], K4[3], Om[3];
-    Phys::K(C, bm, ps.sc[1], pv.q(1, jj), pv.c(1, jj), K1);
+    Phys::K(tv.row(1, tj), bm, bs.vac, bs.scr[1], K1);
     if (kKind == kStagePass && kPass == 0) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) Om[i] = Real(0.5) * h * K1[i];
       rotate(Om, y);
-      Phys::accum(acc, bm.w, pv.q(2, jj), y);
+      Phys::accum(acc, bm.w, Phys::t1(tv.row(2, tj)), y);
       return;
     }
-    Phys::K(C, bm, ps.sc[2], pv.q(2, jj), pv.c(2, jj), K2);
+    Phys::K(tv.row(2, tj), bm, bs.vac, bs.scr[2], K2);
     if (kKind == kStagePass && kPass == 1) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) Om[i] = Real(0.5) * h * K2[i];
       rotate(Om, y);
-      Phys::accum(acc, bm.w, pv.q(3, jj), y);
+      Phys::accum(acc, bm.w, Phys::t1(tv.row(3, tj)), y);
       return;
     }
-    Phys::K(C, bm, ps.sc[3], pv.q(3, jj), pv.c(3, jj), K3);
+    Phys::K(tv.row(3, tj), bm, bs.vac, bs.scr[3], K3);
     if (kKind == kStagePass && kPass == 2) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) Om[i] = Real(0.5) * h * K1[i];
@@ -576,10 +804,10 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
 #pragma unroll
       for (int i = 0; i < 3; ++i) Om[i] = h * K3[i] - Real(0.5) * h * K1[i];
       rotate(Om, y);
-      Phys::accum(acc, bm.w, pv.q(4, jj), y);
+      Phys::accum(acc, bm.w, Phys::t1(tv.row(4, tj)), y);
       return;
     }
-    Phys::K(C, bm, ps.sc[4], pv.q(4, jj), pv.c(4, jj), K4);
+    Phys::K(tv.row(4, tj), bm, bs.vac, bs.scr[4], K4);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
       Om[i] = h * (Real(0.25) * K1[i] + Real(1.0 / 6.0) * (K2[i] + K3[i]) - Real(1.0 / 12.0) * K4[i]);
@@ -589,11 +817,160 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
       Om[i] = h * (Real(-1.0 / 12.0) * K1[i] + Real(1.0 / 6.0) * (K2[i] + K3[i]) + Real(0.25) * K4[i]);
     rotate(Om, y);
     if (mixed) Phys::normalise(y);
-    Phys::accum(acc, bm.w, pv.q(4, jj), y);
+    Phys::accum(acc, bm.w, Phys::t1(tv.row(4, tj)), y);
   }
 };
 
-// Load the beam constants of (species, j, k).
+// ----------------------------------------------------------------------------------------------
+// FP32 two-flavour beams in pairs with packed f32x2 arithmetic (Blackwell fma/mul.rn.f32x2).
+// A thread's two beams are consecutive energy bins of one angle bin, so every table value and step
+// coefficient is shared: it is stored duplicated and loaded as one 64-bit operand, while the
+// per-beam values (state, eta omega, weight) are packed once per pair.  Each packed instruction
+// does the work of two scalar ones, in the same order, so a pair gives the same bits as two
+// scalar beams would with contraction to FMA.
+using F2 = unsigned long long;
+__device__ __forceinline__ F2 pk(float a, float b) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk(F2 r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
+  F2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+  F2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+template <class Tab, int kPass, int kKind>
+struct PairRK {
+  using P = Phys2<float>;
+  static constexpr int kChain =
+      kKind == kInitPass ? 0 : (kKind == kFinalPass ? Tab::S - (Tab::kAdaptive ? 1 : 0) : kPass + 1);
+
+  // K and -K of stage row R (packed values) for the pair's eta omega
+  __device__ static inline void Kpair(const F2* R, F2 eo, F2 (&K)[3], F2 (&nK)[3]) {
+    K[0] = fma2(eo, R[P::vQBX], R[P::vG0X]);
+    K[1] = R[P::vG0Y];
+    K[2] = fma2(eo, R[P::vQBZ], R[P::vG0Z]);
+    nK[0] = fma2(eo, R[P::vNQBX], R[P::vNG0X]);
+    nK[1] = R[P::vNG0Y];
+    nK[2] = fma2(eo, R[P::vNQBZ], R[P::vNG0Z]);
+  }
+  // k = K x Y as K1 Y2 - K2 Y1, ... with the products of -K added by FMA
+  __device__ static inline void cross(const F2 (&K)[3], const F2 (&nK)[3], const F2 (&Y)[3], F2 (&k)[3]) {
+    k[0] = fma2(K[1], Y[2], mul2(nK[2], Y[1]));
+    k[1] = fma2(K[2], Y[0], mul2(nK[0], Y[2]));
+    k[2] = fma2(K[0], Y[1], mul2(nK[1], Y[0]));
+  }
+  __device__ static inline void accum(F2 (&acc)[6], F2 w, F2 t1, const F2 (&y)[3]) {
+    const F2 wt = mul2(w, t1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { acc[i] = fma2(wt, y[i], acc[i]); acc[3 + i] = fma2(w, y[i], acc[3 + i]); }
+  }
+  __device__ static inline void normalise(F2 (&y)[3]) {
+    F2 n2 = mul2(y[0], y[0]);
+    n2 = fma2(y[1], y[1], n2);
+    n2 = fma2(y[2], y[2], n2);
+    float a, b;
+    upk(n2, a, b);
+    const F2 inv = pk(1.0f / sqrtf(a), 1.0f / sqrtf(b));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] = mul2(y[i], inv);
+  }
+
+  // rows: table rows of this pair's angle bin, stage s at rows + s * rstride (in F2 units)
+  template <class BS>
+  __device__ static inline void run(const BS& bs, F2 eo, F2 w, const F2* rows, int rstride, F2 (&y)[3],
+                                    F2 (&acc)[6], float& emax, int& bad) {
+    F2 k[Tab::S + 1][3];
+#pragma unroll
+    for (int l = 1; l <= kChain; ++l) {
+      F2 Y[3] = {y[0], y[1], y[2]};
+#pragma unroll
+      for (int m = 1; m < l; ++m)
+        if (Tab::a(l, m) != 0.0) {
+          const F2 ha = bs.hA2[l][m];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) Y[i] = fma2(ha, k[m][i], Y[i]);
+        }
+      F2 K[3], nK[3];
+      Kpair(rows + l * rstride, eo, K, nK);
+      cross(K, nK, Y, k[l]);
+    }
+    if (kKind == kInitPass) {
+      accum(acc, w, rows[rstride * 1 + P::vT1], y);
+      return;
+    }
+    if (kKind == kStagePass) {
+      constexpr int I = kPass + 2;
+      F2 Y[3] = {y[0], y[1], y[2]};
+#pragma unroll
+      for (int m = 1; m < I; ++m)
+        if (Tab::a(I, m) != 0.0) {
+          const F2 ha = bs.hA2[I][m];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) Y[i] = fma2(ha, k[m][i], Y[i]);
+        }
+      if (Tab::kAdaptive && I == Tab::S) normalise(Y);
+      accum(acc, w, rows[rstride * I + P::vT1], Y);
+      return;
+    }
+    // final pass
+    F2 yn[3] = {y[0], y[1], y[2]};
+#pragma unroll
+    for (int m = 1; m <= kChain; ++m)
+      if (Tab::b(m) != 0.0) {
+        const F2 hb = bs.hB2[m];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) yn[i] = fma2(hb, k[m][i], yn[i]);
+      }
+    float a0[3], a1[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) upk(yn[i], a0[i], a1[i]);
+    const bool ok0 = 0.5f * (a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]) <= 3.0e38f;
+    const bool ok1 = 0.5f * (a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]) <= 3.0e38f;
+    if (ok0 && ok1) normalise(yn);
+    if (Tab::kAdaptive) {
+      float y0[3], y1[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) upk(y[i], y0[i], y1[i]);
+      if (!(P::tnorm2(y0) <= 3.0e38f) || !(P::tnorm2(y1) <= 3.0e38f)) bad = 1;
+      F2 K[3], nK[3];
+      Kpair(rows + Tab::S * rstride, eo, K, nK);
+      cross(K, nK, yn, k[Tab::S]);
+      F2 e[3] = {0ull, 0ull, 0ull};
+#pragma unroll
+      for (int m = 1; m <= Tab::S; ++m)
+        if (Tab::e(m) != 0.0) {
+          const F2 he = bs.hE2[m];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) e[i] = fma2(he, k[m][i], e[i]);
+        }
+      float e0[3], e1[3], n0[3], n1[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { upk(e[i], e0[i], e1[i]); upk(yn[i], n0[i], n1[i]); }
+      const float atol = bs.atol, rtol = bs.rtol;
+      float r0 = P::enorm(e0) / (atol + rtol * sqrtf(fmaxf(P::tnorm2(y0), P::tnorm2(n0))));
+      float r1 = P::enorm(e1) / (atol + rtol * sqrtf(fmaxf(P::tnorm2(y1), P::tnorm2(n1))));
+      if (!(r0 <= 3.0e38f) || !ok0) r0 = INFINITY;
+      if (!(r1 <= 3.0e38f) || !ok1) r1 = INFINITY;
+      emax = fmaxf(emax, fmaxf(r0, r1));
+    } else {
+      accum(acc, w, rows[rstride * Tab::S + P::vT1], yn);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] = yn[i];
+  }
+};
+
+// Load the beam constants of (species, energy k) and the angle weight du.
 template <typename Real>
 __device__ __forceinline__ void load_beam(const Real* et, int ne, int sigma, int k, Real du,
                                           typename Phys2<Real>::Beam& bm) {
@@ -610,67 +987,80 @@ __device__ __forceinline__ void load_beam(const Real* et, int ne, int sigma, int
   bm.w = du * et[(2 + sigma) * ne + k];
 }
 
-template <typename Real, int NSC>
-struct BlockShared {
-  Real sc[kMaxStages][NSC];
-  Real hA[kMaxStages][kMaxStages];
-  Real hB[kMaxStages];
-  Real hE[kMaxStages];
-  Real Cv[12];
-  Real rtol, atol;
-  double fx[kNMMax];
-  int active;
-  int parity;
-  int flag;
-};
+// Stages whose table rows a pass reads (bit s set: row s needed).
+template <class Tab, int kPass, int kKind>
+__device__ __forceinline__ unsigned stages_needed() {
+  if (kKind == kInitPass) return 1u << 1;
+  if (kKind == kFinalPass) return ((1u << (Tab::S + 1)) - 1u) & ~1u;          // 1..S
+  return ((1u << (kPass + 3)) - 1u) & ~1u;                                      // 1..kPass+2
+}
 
 // One pass over all pieces of this block.
 template <class Phys, class Tab, typename Real, bool kCF, int kPass, int kKind>
-__device__ void run_pass(const KParams& p, BlockShared<Real, Phys::NSC>& bs, unsigned char* dyn_smem) {
+__device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned char* dyn_smem) {
   constexpr int NC = Phys::NC, NM = Phys::NM, VN = Vec16<Real>::N;
   using Body = PassBody<Phys, Tab, Real, kCF, kPass, kKind>;
   double* red = reinterpret_cast<double*>(dyn_smem);                 // 32 * NM doubles
-  Real* cq = reinterpret_cast<Real*>(red + 32 * kNMMax);             // [kMaxStages][max_jj][2]
-  Real* dut = cq + (size_t)kMaxStages * p.max_jj * 2;                 // [max_jj]
+  Real* tab = reinterpret_cast<Real*>(red + 32 * kNMMax);            // [kMaxStages][max_jj][KT]
+  Real* dut = tab + (size_t)kMaxStages * p.max_jj * Phys::KT;        // [max_jj]
   const bool mixed = sizeof(Real) == 4;
-  const int slot = kKind == kInitPass ? 1 : (kKind == kStagePass ? kPass + 2 : Tab::S);
+  const int slot = kKind == kInitPass ? 1 : (kKind == kStagePass ? kPass + 2 : 0);
+  // Clear the accumulator slot the previous barrier consumed (block 0, while the other blocks
+  // already work): before pass 0 the slots of the previous final pass (0) and of the initial
+  // reduction (1), before pass p the slot of stage p + 1.  Nothing accumulates into these slots
+  // until several barriers later, and block 0's stores are fenced at its next arrival.
+  if (kKind != kInitPass && blockIdx.x == 0) {
+    constexpr int kWords = kAccCopies * kNMMax * 2;
+    for (int t = threadIdx.x; t < p.n_inst * 2 * kWords; t += blockDim.x) {
+      const int inst = t / (2 * kWords), rem = t % (2 * kWords);
+      const int zslot = kPass == 0 ? (rem < kWords ? 0 : 1) : (rem < kWords ? kPass + 1 : -1);
+      if (zslot >= 0) p.acc[(size_t)inst * kAccWordsPerInst + (size_t)zslot * kWords + rem % kWords] = 0ull;
+    }
+  }
+  const unsigned need = stages_needed<Tab, kPass, kKind>();
   const int b0 = p.blk_piece[blockIdx.x], b1 = p.blk_piece[blockIdx.x + 1];
   for (int pi = b0; pi < b1; ++pi) {
     const Piece pc = p.pieces[pi];
     const InstConst& ic = p.ic[pc.inst];
     const InstDyn* d = p.dyn + pc.inst;
     __syncthreads();
+    // one parallel load phase: flags, step size, stage constants, radii, angle weights
     if (threadIdx.x == 0) {
       bs.active = (ldcg(&d->done) == 0 && ldcg(&d->status) == 0) ? 1 : 0;
       bs.parity = ldcg(&d->parity);
     }
-    __syncthreads();
-    if (!bs.active) continue;
-    // stage constants, step coefficients and geometry tables of this piece
     const double h = Tab::kAdaptive ? ldcg(&d->h) : ldcg(&d->h_fixed);
     for (int t = threadIdx.x; t < kMaxStages * Phys::NSC; t += blockDim.x) {
       const int s = t / Phys::NSC, c = t % Phys::NSC;
-      bs.sc[s][c] = (Real)ldcg(&d->sc[s][c]);
+      const double v = ((need >> s) & 1u) ? ldcg(&d->sc[s][c]) : 0.0;
+      bs.scd[s][c] = v;
+      bs.scr[s][c] = (Real)v;
     }
+    if (threadIdx.x < kMaxStages) bs.xs[threadIdx.x] = ldcg(&d->xs[threadIdx.x]);
     if (threadIdx.x < kMaxStages * kMaxStages) {
       const int i = threadIdx.x / kMaxStages, j = threadIdx.x % kMaxStages;
-      if constexpr (!kCF) bs.hA[i][j] = (Real)(h * ((i >= 1 && j >= 1) ? Tab::a(i, j) : 0.0));
+      bs.hA[i][j] = (Real)(h * ((i >= 1 && j >= 1) ? Tab::a(i, j) : 0.0));
+      const float fa = (float)bs.hA[i][j];
+      bs.hA2[i][j] = pk(fa, fa);
     }
     if (threadIdx.x < kMaxStages) {
       const int i = threadIdx.x;
-      if constexpr (!kCF) {
+      if (kCF) {
+        bs.hB[i] = (Real)h;
+        bs.hE[i] = 0;
+      } else {
         bs.hB[i] = (Real)(h * (i >= 1 ? Tab::b(i) : 0.0));
         bs.hE[i] = (Real)(h * (i >= 1 ? Tab::e(i) : 0.0));
-      } else {
-        bs.hB[i] = (Real)h;
       }
+      const float fb = (float)bs.hB[i], fe = (float)bs.hE[i];
+      bs.hB2[i] = pk(fb, fb);
+      bs.hE2[i] = pk(fe, fe);
+    }
+    if (threadIdx.x < 6) {
+      bs.vac[threadIdx.x] = (Real)ic.M21[threadIdx.x];
+      bs.vac[6 + threadIdx.x] = (Real)ic.M31[threadIdx.x];
     }
     if (threadIdx.x == 0) {
-      if constexpr (Phys::NC == 3) {
-        bs.Cv[0] = (Real)ic.B[0]; bs.Cv[1] = (Real)ic.B[1]; bs.Cv[2] = (Real)ic.B[2];
-      } else {
-        for (int i = 0; i < 6; ++i) { bs.Cv[i] = (Real)ic.M21[i]; bs.Cv[6 + i] = (Real)ic.M31[i]; }
-      }
       bs.rtol = (Real)ic.rtol;
       bs.atol = (Real)ic.atol;
     }
@@ -680,23 +1070,31 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys::NSC>& bs, uns
       const int j = jj >= (int)ic.n_angle ? jj - (int)ic.n_angle : jj;
       dut[t] = (Real)p.du_tab[ic.a_off + j];
     }
-    for (int t = threadIdx.x; t < Tab::S * n_jj; t += blockDim.x) {
-      const int s = 1 + t / n_jj, tj = t % n_jj;
-      const int jj = pc.jj_lo + tj;
-      const int j = jj >= (int)ic.n_angle ? jj - (int)ic.n_angle : jj;
-      const double c = sqrt(1.0 - p.u_tab[ic.a_off + j] * ldcg(&d->xs[s]));
-      cq[(s * n_jj + tj) * 2] = (Real)c;
-      cq[(s * n_jj + tj) * 2 + 1] = (Real)(1.0 / c);
-    }
     __syncthreads();
+    if (!bs.active) continue;
     typename Phys::Consts C;
     if constexpr (Phys::NC == 3) {
-      C.B[0] = bs.Cv[0]; C.B[1] = bs.Cv[1]; C.B[2] = bs.Cv[2];
+      C.B[0] = ic.B[0]; C.B[1] = ic.B[1]; C.B[2] = ic.B[2];
     } else {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) { C.M21[i] = bs.Cv[i]; C.M31[i] = bs.Cv[6 + i]; }
+      for (int i = 0; i < 6; ++i) { C.M21[i] = ic.M21[i]; C.M31[i] = ic.M31[i]; }
     }
-    const PieceView<Real, Phys> pv{cq, dut, n_jj};
+    for (int t = threadIdx.x; t < kMaxStages * n_jj; t += blockDim.x) {
+      const int s = t / n_jj, tj = t % n_jj;
+      if (!((need >> s) & 1u)) continue;
+      const int jj = pc.jj_lo + tj;
+      const int j = jj >= (int)ic.n_angle ? jj - (int)ic.n_angle : jj;
+      Real* row = tab + ((size_t)s * n_jj + tj) * Phys::KT;
+      if constexpr (sizeof(Real) == 4) {
+        float q, t1, t2;
+        geometry_f(p.u_tab[ic.a_off + j], bs.xs[s], q, t1, t2);
+        Phys::fill_f(row, q, t1, t2, bs.scr[s], C);
+      } else {
+        Phys::fill(row, geometry(p.u_tab[ic.a_off + j], bs.xs[s]), bs.scd[s], C);
+      }
+    }
+    __syncthreads();
+    const TabView<Real, Phys> tv{tab, n_jj};
     const Real* et = reinterpret_cast<const Real*>(p.etab) + ic.e_off;
     const Real* yin = reinterpret_cast<const Real*>(bs.parity ? p.planeB : p.planeA) + ic.beam_off;
     Real* yout = reinterpret_cast<Real*>(bs.parity ? p.planeA : p.planeB) + ic.beam_off;
@@ -706,35 +1104,134 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys::NSC>& bs, uns
     for (int i = 0; i < NM; ++i) acc[i] = 0;
     Real emax = 0;
     int bad = 0;
+    // FP32 two-flavour RK passes run beam pairs on packed f32x2 arithmetic (PairRK)
+    constexpr bool kPair = sizeof(Real) == 4 && NC == 3 && !kCF;
+    F2 acc2[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    float emax2 = 0.0f;
     const uint32_t end = pc.start + pc.len;
-    for (uint32_t l0 = pc.start + VN * threadIdx.x; l0 < end; l0 += VN * blockDim.x) {
-      Real ys[NC][VN];
+    const uint32_t vstep = VN * blockDim.x;
+    // two flavours: the next vector's state is loaded while this one is processed, so the L2/HBM
+    // latency of the stream overlaps the arithmetic
+    constexpr bool kPrefetch = NC == 3;
+    Real nxt[NC][VN];
+    if (kPrefetch && pc.start + VN * threadIdx.x < end) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) vload(yin + (size_t)c * p.plane_stride + l0, ys[c]);
+      for (int c = 0; c < NC; ++c) vload(yin + (size_t)c * p.plane_stride + pc.start + VN * threadIdx.x, nxt[c]);
+    }
+    for (uint32_t l0 = pc.start + VN * threadIdx.x; l0 < end; l0 += vstep) {
+      Real ys[NC][VN];
+      if constexpr (kPrefetch) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+          for (int v = 0; v < VN; ++v) ys[c][v] = nxt[c][v];
+        if (l0 + vstep < end) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) vload(yin + (size_t)c * p.plane_stride + l0 + vstep, nxt[c]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) vload(yin + (size_t)c * p.plane_stride + l0, ys[c]);
+      }
       int jj = (int)fast_div(l0, ic.div_magic);
       int k = (int)l0 - jj * ne;
-#pragma unroll
-      for (int v = 0; v < VN; ++v) {
-        if (l0 + v < end) {
+      bool paired = false;
+      if constexpr (kPair) {
+        // both beams in the same angle bin (all but the rare pair that straddles two bins)
+        if (l0 + 1 < end && k + 1 < ne) {
+          paired = true;
           const int sigma = jj >= na ? 1 : 0;
-          typename Phys::Beam bm;
-          load_beam<Real>(et, ne, sigma, k, dut[jj - (int)pc.jj_lo], bm);
-          Real y[NC];
+          const int tj = jj - (int)pc.jj_lo;
+          typename Phys2<float>::Beam b0, b1;
+          load_beam<float>(et, ne, sigma, k, dut[tj], b0);
+          load_beam<float>(et, ne, sigma, k + 1, dut[tj], b1);
+          F2 y2[3];
 #pragma unroll
-          for (int c = 0; c < NC; ++c) y[c] = ys[c][v];
-          Body::beam(bs, C, bm, pv, jj - (int)pc.jj_lo, y, acc, emax, bad, mixed);
+          for (int c = 0; c < 3; ++c) y2[c] = pk(ys[c][0], ys[c][1]);
+          const F2* rows = reinterpret_cast<const F2*>(tab) + (size_t)tj * (Phys::KT / 2);
+          PairRK<Tab, kPass, kKind>::run(bs, pk(b0.eo, b1.eo), pk(b0.w, b1.w), rows,
+                                         n_jj * (Phys::KT / 2), y2, acc2, emax2, bad);
 #pragma unroll
-          for (int c = 0; c < NC; ++c) ys[c][v] = y[c];
+          for (int c = 0; c < 3; ++c) upk(y2[c], ys[c][0], ys[c][1]);
         }
-        if (++k == ne) { k = 0; ++jj; }
+      }
+      if (!paired) {
+#pragma unroll
+        for (int v = 0; v < VN; ++v) {
+          if (l0 + v < end) {
+            const int sigma = jj >= na ? 1 : 0;
+            const int tj = jj - (int)pc.jj_lo;
+            typename Phys::Beam bm;
+            load_beam<Real>(et, ne, sigma, k, dut[tj], bm);
+            Real y[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) y[c] = ys[c][v];
+            Body::beam(bs, bm, tv, tj, y, acc, emax, bad, mixed);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ys[c][v] = y[c];
+          }
+          if (++k == ne) { k = 0; ++jj; }
+        }
       }
       if (kKind == kFinalPass) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) vstore(yout + (size_t)c * p.plane_stride + l0, ys[c]);
       }
     }
+    if constexpr (kPair) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        float a, b;
+        upk(acc2[i], a, b);
+        acc[i] += a + b;
+      }
+      emax = fmax(emax, (Real)emax2);
+    }
     // reduce this piece into the instance accumulators
-    if (kKind == kFinalPass && Tab::kAdaptive) {
+    if constexpr (sizeof(Real) == 4) {
+      // mixed precision: warp trees in FP32, the warps' partials summed in a fixed order, and the
+      // block's partial added to one of the instance's accumulator copies as a fixed-point integer
+      // (integer atomics: order-independent; no FP64 instruction)
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      float* redf = reinterpret_cast<float*>(red);
+      if (kKind == kFinalPass && Tab::kAdaptive) {
+        float em = (emax <= 3.0e38f) ? (float)emax : INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) em = fmaxf(em, __shfl_down_sync(0xffffffffu, em, o));
+        if (lane == 0) redf[warp] = em;
+        const int any_bad = __syncthreads_or(bad);
+        if (threadIdx.x == 0) {
+          float m = 0.0f;
+          for (int w = 0; w < nw; ++w) m = fmaxf(m, redf[w]);
+          if (any_bad) atomicExch(&p.nonfinite[pc.inst], 1);
+          atomicMax(&p.errmax[pc.inst], (unsigned long long)__double_as_longlong((double)m));
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < NM; ++i)
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
+        if (lane == 0) {
+#pragma unroll
+          for (int i = 0; i < NM; ++i) redf[warp * NM + i] = (float)acc[i];
+        }
+        __syncthreads();
+        if (threadIdx.x < NM) {
+          float sum = 0.0f;
+          for (int w = 0; w < nw; ++w) sum += redf[w * NM + threadIdx.x];
+          long long fx;
+          unsigned long long* a = p.acc + (size_t)pc.inst * kAccWordsPerInst +
+                                  (((size_t)slot * kAccCopies + blockIdx.x % kAccCopies) * kNMMax + threadIdx.x) * 2;
+          if (f32_to_fix48(sum, fx)) {
+            atomicAdd(a, (unsigned long long)fx);
+          } else if (Tab::kAdaptive && kKind == kStagePass) {
+            atomicMax(&p.errmax[pc.inst], 0x7ff0000000000000ull);   // overflowing trial step
+          } else {
+            atomicExch(&p.nonfinite[pc.inst], 1);
+          }
+        }
+      }
+    } else if (kKind == kFinalPass && Tab::kAdaptive) {
       const double em = (emax <= rbig<Real>()) ? (double)emax : __longlong_as_double(0x7ff0000000000000ll);
       const int any_bad = __syncthreads_or(bad);
       const double bmax = block_max(em, red);
@@ -762,7 +1259,8 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys::NSC>& bs, uns
       }
       __syncthreads();
       if (bs.flag && threadIdx.x < NM) {
-        unsigned long long* a = p.acc + (((size_t)pc.inst * kMaxStages + slot) * kNMMax + threadIdx.x) * 2;
+        unsigned long long* a = p.acc + (size_t)pc.inst * kAccWordsPerInst +
+                                (((size_t)slot * kAccCopies + blockIdx.x % kAccCopies) * kNMMax + threadIdx.x) * 2;
         fx_add(a, bs.fx[threadIdx.x]);
       }
     }
@@ -770,28 +1268,47 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys::NSC>& bs, uns
 }
 
 template <class Phys, class Tab, typename Real, bool kCF, int kPass>
-__device__ __forceinline__ bool pass_and_sync(const KParams& p, BlockShared<Real, Phys::NSC>& bs,
+__device__ __forceinline__ bool pass_and_sync(const KParams& p, BlockShared<Real, Phys>& bs,
                                               unsigned char* dyn_smem) {
   constexpr bool kFinal = kPass == Tab::kPasses - 1;
   constexpr int kKind = kFinal ? kFinalPass : kStagePass;
+  unsigned long long t0 = 0, t1 = 0;
+  if (p.trace && threadIdx.x == 0) t0 = globaltimer_ns();
   run_pass<Phys, Tab, Real, kCF, kPass, kKind>(p, bs, dyn_smem);
-  const bool last = barrier_arrive(p.bar, gridDim.x, p.timeout_ns, p.status, &bs.flag);
-  if (last) {
-    __threadfence();
-    serial_update<Phys, Tab>(p, kFinal ? Tab::S : kPass + 2, kFinal, false);
-    __syncthreads();
-    if (kFinal && threadIdx.x == 0) {
-      int all = 1;
-      for (int i = 0; i < p.n_inst; ++i) all &= (p.dyn[i].done || p.dyn[i].status) ? 1 : 0;
-      *p.all_done = all;
+  if (p.trace && threadIdx.x == 0) t1 = globaltimer_ns();
+  const int res = barrier_arrive(p.bar, gridDim.x, p.timeout_ns, p.status, &bs.flag, &bs.gen_seen);
+  if ((res & 0xf) == kBarAbort) return false;
+  if (p.trace && threadIdx.x == 0) {
+    const int idx = bs.pass_idx++;
+    if (idx < p.trace_passes) {
+      unsigned long long* t = p.trace + ((size_t)idx * gridDim.x + blockIdx.x) * 4;
+      t[0] = t0;
+      t[1] = t1;
+      t[2] = globaltimer_ns();
+      t[3] = (res & 0xf) == kBarLast ? 1ull : 0ull;
     }
-    barrier_release(p.bar);
   }
-  return !barrier_aborted(p.bar, &bs.flag);
+  if ((res & 0xf) == kBarLast) {
+    const int mine = serial_update<Phys, Tab, Real>(p, kFinal ? 0 : kPass + 2, kFinal, false);
+    const int all = __syncthreads_and(mine);
+    if (kFinal) serial_geometry<Tab>(p);
+    if (threadIdx.x == 0) {
+      if (kFinal) *p.all_done = all;
+      bs.flag = (kFinal && all) ? 0x10 : 0;
+    }
+    unsigned long long ts = 0;
+    if (p.trace && threadIdx.x == 0) ts = globaltimer_ns();
+    barrier_release(p.bar, kFinal ? all : 0, &bs.gen_seen);
+    if (p.trace && threadIdx.x == 0 && bs.pass_idx - 1 < p.trace_passes) {
+      // last block: stamp 3 = serial work done (bits 0..62), stamp 2 stays its arrival
+      p.trace[((size_t)(bs.pass_idx - 1) * gridDim.x + blockIdx.x) * 4 + 3] = ts | (1ull << 63);
+    }
+  }
+  return true;
 }
 
 template <class Phys, class Tab, typename Real, bool kCF, int kPass>
-__device__ __forceinline__ bool all_passes(const KParams& p, BlockShared<Real, Phys::NSC>& bs,
+__device__ __forceinline__ bool all_passes(const KParams& p, BlockShared<Real, Phys>& bs,
                                            unsigned char* dyn_smem) {
   if constexpr (kPass < Tab::kPasses) {
     if (!pass_and_sync<Phys, Tab, Real, kCF, kPass>(p, bs, dyn_smem)) return false;
@@ -801,32 +1318,35 @@ __device__ __forceinline__ bool all_passes(const KParams& p, BlockShared<Real, P
   }
 }
 
-template <class Phys, class Tab, typename Real, bool kCF>
-__global__ void __launch_bounds__(512) step_kernel(KParams p) {
+// kMinB: resident 256-thread blocks per SM the register budget is sized for.  FP64 work runs on
+// GB300's narrow FP64 pipe (about 1/68 of the FP32 rate), which one block per SM already keeps
+// busy, so FP64 kernels are built with kMinB = 1 (whole register file, no spills).  The FP32
+// two-flavour kernels are latency-bound; they are built for 2 and 3 blocks per SM and the launch
+// shape is chosen by measurement (the autotuner in paper_1912_10596_gb300/autotune.py).
+template <class Phys, class Tab, typename Real, bool kCF, int kMinB>
+__global__ void __launch_bounds__(256, kMinB) step_kernel(KParams p) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  __shared__ BlockShared<Real, Phys::NSC> bs;
+  __shared__ BlockShared<Real, Phys> bs;
+  if (threadIdx.x == 0) {
+    bs.pass_idx = 0;
+    bs.gen_seen = ld_acquire(&p.bar->gen);        // later barriers track the generation locally
+  }
   if (p.init_only) {
     run_pass<Phys, Tab, Real, kCF, 0, kInitPass>(p, bs, dyn_smem);
-    const bool last = barrier_arrive(p.bar, gridDim.x, p.timeout_ns, p.status, &bs.flag);
-    if (last) {
-      __threadfence();
-      serial_update<Phys, Tab>(p, 1, false, true);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int all = 1;
-        for (int i = 0; i < p.n_inst; ++i) all &= (p.dyn[i].done || p.dyn[i].status) ? 1 : 0;
-        *p.all_done = all;
-      }
-      barrier_release(p.bar);
+    const int res = barrier_arrive(p.bar, gridDim.x, p.timeout_ns, p.status, &bs.flag, &bs.gen_seen);
+    if ((res & 0xf) == kBarLast) {
+      const int mine = serial_update<Phys, Tab, Real>(p, 1, false, true);
+      const int all = __syncthreads_and(mine);
+      serial_geometry<Tab>(p);
+      if (threadIdx.x == 0) *p.all_done = all;
+      barrier_release(p.bar, 0, &bs.gen_seen);
     }
     return;
   }
   for (int step = 0; step < p.n_steps; ++step) {
     if (!all_passes<Phys, Tab, Real, kCF, 0>(p, bs, dyn_smem)) return;
-    __syncthreads();
-    if (threadIdx.x == 0) bs.flag = ldcg(p.all_done);
-    __syncthreads();
-    if (bs.flag) return;
+    // the release of the final pass carried "every instance finished" in bit 4 of bs.flag
+    if (bs.flag & 0x10) return;
   }
 }
 

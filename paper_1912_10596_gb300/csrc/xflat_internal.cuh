@@ -20,6 +20,12 @@ constexpr int kNSC2 = 8;            // stage constants: mu*j0 (3), mu*j1 (3), la
 constexpr int kNSC3 = 20;           // mu*j0 (9), mu*j1 (9), lambda, R^2/r^2
 constexpr int kNMMax = 18;
 constexpr int kNSCMax = 20;
+// Blocks add their moment partials to one of kAccCopies copies of an instance's accumulators
+// (block index mod kAccCopies), so the integer atomics of hundreds of blocks spread over several
+// L2 lines instead of queueing on one; the last block sums the copies (exact integer sums).
+constexpr int kAccCopies = 8;
+// accumulator words per instance: [stage slot][copy][component][2]
+constexpr int kAccWordsPerInst = kMaxStages * kAccCopies * kNMMax * 2;
 
 enum Integrator : int { kRK4 = 0, kDP45 = 1, kLieRK4 = 2 };
 enum Matter : int { kMatterNone = 0, kMatterPower = 1, kMatterConst = 2 };
@@ -51,7 +57,10 @@ struct InstDyn {
   double err;               // last error norm
   double rs[kMaxStages];    // stage radii of the current step
   double xs[kMaxStages];    // R^2 / rs^2
+  double mus[kMaxStages];   // mu(rs): nu-nu strength at the stage radii
+  double lams[kMaxStages];  // lambda(rs): matter strength at the stage radii
   int32_t status, done, last, parity;
+  int32_t geo_pending, pad_geo;   // stage geometry of the next step still to be computed
   unsigned long long accepted, rejected, stage_evals;
   double mom[kMaxStages][kNMMax];   // raw moments (weights normalised by wscale) per stage
   double sc[kMaxStages][kNSCMax];   // stage constants per stage
@@ -143,47 +152,61 @@ __device__ __forceinline__ double block_max(double v, double* scratch) {
   return v;
 }
 
-// Device-wide barrier.  Returns true in every thread of the one block that arrived last (that
-// block must call barrier_release after its serial work); false elsewhere, after the release.
-// Every wait is bounded by timeout_ns: on expiry the block records XFLAT_ERR_TIMEOUT in *status_word,
-// raises the abort flag and returns false; callers check barrier_aborted() after every barrier.
-__device__ __forceinline__ bool barrier_arrive(Barrier* bar, unsigned int n_blocks,
-                                              unsigned long long timeout_ns, int* status_word,
-                                              int* s_flag) {
+// Device-wide barrier.  Returns kBarLast in every thread of the one block that arrived last (that
+// block must call barrier_release after its serial work), kBarReleased elsewhere after the
+// release, or kBarAbort.  Every wait is bounded by timeout_ns: on expiry the block records
+// XFLAT_ERR_TIMEOUT in *status_word, raises the abort flag and returns kBarAbort; a block that sees
+// the abort flag while waiting also returns kBarAbort, so every block leaves the kernel.
+enum BarrierResult : int { kBarReleased = 0, kBarLast = 1, kBarAbort = 2 };
+
+__device__ __forceinline__ int barrier_arrive(Barrier* bar, unsigned int n_blocks,
+                                             unsigned long long timeout_ns, int* status_word,
+                                             int* s_flag, unsigned int* s_gen) {
+  // *s_gen: in, the generation this block last saw; out (released blocks), the new one
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int g = ld_acquire(&bar->gen);
-    __threadfence();
+    const unsigned int g = *s_gen;                 // generation of the last barrier this block passed
+    __threadfence();                               // this block's writes before its arrival
     const unsigned int ticket = atomicAdd(&bar->count, 1u);
     const unsigned int expected = n_blocks + bar->extra;
-    int last = (ticket == expected - 1) ? 1 : 0;
-    if (!last) {
+    int res = (ticket == expected - 1) ? kBarLast : kBarReleased;
+    unsigned int gnow = g;
+    if (res == kBarLast) {
+      __threadfence();                             // acquire: every other block's writes
+    } else {
       const unsigned long long t0 = globaltimer_ns();
-      while (ld_acquire(&bar->gen) == g) {
-        if (ld_acquire_int(&bar->abort)) break;
+      while ((gnow = ld_acquire(&bar->gen)) == g) {   // acquire load: no further fence needed
+        if (ld_acquire_int(&bar->abort)) { res = kBarAbort; break; }
         if (globaltimer_ns() - t0 > timeout_ns) {
           atomicAdd(&bar->timeout_hits, 1);
           atomicCAS(status_word, 0, 4 /* XFLAT_ERR_TIMEOUT */);
           atomicExch(&bar->abort, 1);
+          res = kBarAbort;
           break;
         }
-        __nanosleep(32);
+        __nanosleep(20);
       }
     }
-    __threadfence();
-    *s_flag = last;
+    if (res == kBarReleased) *s_gen = gnow;
+    *s_flag = res | (int)((gnow & 1u) << 4);       // bit 4: the flag carried by the release
   }
   __syncthreads();
-  return *s_flag != 0;
+  return *s_flag;
 }
 
-__device__ __forceinline__ void barrier_release(Barrier* bar) {
-  __threadfence();
+// Release the barrier (last block only, after its serial work; every thread that wrote shared
+// results must have executed __threadfence() before the __syncthreads here).  The generation word
+// advances by 2 and its low bit carries one flag to every waiting block (the kernels use it for
+// "every instance finished"), so a released block learns it from the load that saw the release.
+// The count is reset before the new generation is published with release ordering.
+__device__ __forceinline__ void barrier_release(Barrier* bar, int flag, unsigned int* s_gen) {
   __syncthreads();
   if (threadIdx.x == 0) {
     bar->count = 0;
-    __threadfence();
-    atomicAdd(&bar->gen, 1u);
+    const unsigned int ng = ((*s_gen & ~1u) + 2u) | (flag ? 1u : 0u);
+    *s_gen = ng;
+    unsigned int old;
+    asm volatile("atom.release.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(&bar->gen), "r"(ng) : "memory");
   }
 }
 

@@ -81,6 +81,7 @@ _SIGS = {
     "xflat_debug_barrier_extra": (_H, C.c_uint32),
     "xflat_moments_2f_noalloc": (_P, C.c_uint32, C.c_uint32, _P, _P, _P, C.c_double, C.c_double,
                                  _P, _P),
+    "xflat_debug_trace": (_H, C.c_uint32, _P, C.POINTER(C.c_uint32)),
 }
 NOALLOC_MAX_ANGLES = 4096
 for _name, _args in _SIGS.items():
