@@ -257,3 +257,12 @@ def random_unit_states(n_flavor: int, n_beams: int, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(Xoshiro256ss(seed).next_u64()))
     z = rng.standard_normal((n_beams, n_flavor)) + 1j * rng.standard_normal((n_beams, n_flavor))
     return z / np.linalg.norm(z, axis=1, keepdims=True)
+
+
+def coherent_unit_states(n_flavor: int, n_beams: int, seed: int, spread: float = 0.3) -> np.ndarray:
+    """Random pure states clustered around one common state (1, 0.4, [0.2]) / norm: every beam
+    carries the same flavour coherence up to a random spread, so the angular moments are of
+    the order of the total weight (unlike independent random states, whose moments cancel)."""
+    base = np.array([1.0, 0.4, 0.2][:n_flavor], dtype=np.complex128)
+    z = base[None, :] + spread * random_unit_states(n_flavor, n_beams, seed)
+    return z / np.linalg.norm(z, axis=1, keepdims=True)

@@ -184,6 +184,15 @@ int xflat_evolve_batch(xflat_t h, const double* r1_km_per_instance);
  * one call behind; xflat_get_stats gives the exact state after synchronising. */
 int xflat_advance(xflat_t h, const double* r1_km_per_instance, uint32_t max_steps, int* done_out);
 
+/* Enqueue n_launches further xflat_advance(h, NULL, max_steps) launches as ONE CUDA graph launch on
+ * the handle's stream.  The graph (the persistent launches and the read-back of the status words)
+ * is captured on first use for this (n_launches, max_steps) pair and kept by the handle until the
+ * pair changes or the handle is destroyed.  The previous call that touched the state must have
+ * been xflat_advance or xflat_advance_graph (else XFLAT_ERR_STATE): the graph continues toward the
+ * targets set there.  No host synchronisation; *done_out (nullable) as for xflat_advance.
+ * XFLAT_ERR_CUDA if the capture fails. */
+int xflat_advance_graph(xflat_t h, uint32_t n_launches, uint32_t max_steps, int* done_out);
+
 /* ---- outputs ----------------------------------------------------------------------------------- */
 
 /* Traceless parts of the two beam-independent moments of the current state at the current radius:

@@ -130,8 +130,10 @@ def evolve_fixed(bulb, Y0, r0, r1, n_steps, method="rk4", callback=None):
     return Y, st
 
 
-def evolve_adaptive(bulb, Y0, r0, r1, rtol, atol, h0, h_min=1e-14, h_max=np.inf, max_steps=10**7):
-    """Adaptive Dormand-Prince 5(4) with the controller in the module docstring."""
+def evolve_adaptive(bulb, Y0, r0, r1, rtol, atol, h0, h_min=1e-14, h_max=np.inf, max_steps=10**7,
+                    max_attempts=None):
+    """Adaptive Dormand-Prince 5(4) with the controller in the module docstring.  With
+    max_attempts, stop after that many attempted steps (accepted or rejected) short of r1."""
     f = bulb.rhs
     Y = Y0.copy()
     r = r0
@@ -160,4 +162,6 @@ def evolve_adaptive(bulb, Y0, r0, r1, rtol, atol, h0, h_min=1e-14, h_max=np.inf,
             raise FloatingPointError(f"step size underflow at r={r}: h={h}")
         if st.accepted + st.rejected > max_steps:
             raise RuntimeError("too many steps")
+        if max_attempts is not None and st.accepted + st.rejected >= max_attempts:
+            break
     return Y, r, st

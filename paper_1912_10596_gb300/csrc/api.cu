@@ -82,6 +82,9 @@ struct xflat_s {
   uint32_t debug_extra = 0;
   unsigned long long* d_trace = nullptr;   // pass trace (xflat_debug_trace)
   uint32_t trace_passes = 0;
+  cudaGraph_t graph = nullptr;             // captured launches of xflat_advance_graph
+  cudaGraphExec_t graph_exec = nullptr;
+  uint32_t graph_launches = 0, graph_steps = 0;
   bool moments_valid = false;
   bool advancing = false;                  // last call was an xflat_advance launch
   std::string err;
@@ -436,14 +439,14 @@ KParams make_params(xflat_t h, int n_steps, int init_only) {
   return p;
 }
 
-int launch(xflat_t h, int n_steps, int init_only) {
+int launch(xflat_t h, int n_steps, int init_only, cudaStream_t stream) {
   KParams p = make_params(h, n_steps, init_only);
   void* args[] = {&p};
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(h->grid);
   cfg.blockDim = dim3(h->block);
   cfg.dynamicSmemBytes = h->smem;
-  cfg.stream = h->stream;
+  cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
@@ -451,6 +454,52 @@ int launch(xflat_t h, int n_steps, int init_only) {
   cfg.numAttrs = 1;
   CUDA_TRY(h, cudaLaunchKernelExC(&cfg, h->kernel, args));
   h->launches++;
+  return XFLAT_OK;
+}
+int launch(xflat_t h, int n_steps, int init_only) { return launch(h, n_steps, init_only, h->stream); }
+
+void drop_graph(xflat_t h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->graph_exec = nullptr;
+  h->graph = nullptr;
+  h->graph_launches = h->graph_steps = 0;
+}
+
+// Capture n_launches persistent launches of max_steps steps each, followed by the read-back of the
+// status words, into one executable graph.  Capture runs on a private stream (the legacy default
+// stream cannot be captured); the graph is launched on the handle's stream.
+int capture_graph(xflat_t h, uint32_t n_launches, uint32_t max_steps) {
+  drop_graph(h);
+  cudaStream_t cs = nullptr;
+  CUDA_TRY(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  const uint64_t launches0 = h->launches;
+  int rc = XFLAT_OK;
+  if (e == cudaSuccess) {
+    for (uint32_t i = 0; i < n_launches && rc == XFLAT_OK; ++i) rc = launch(h, (int)max_steps, 0, cs);
+    if (rc == XFLAT_OK)
+      e = cudaMemcpyAsync(h->h_words, h->d_words, 2 * sizeof(int), cudaMemcpyDeviceToHost, cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (rc == XFLAT_OK && e == cudaSuccess) {
+      h->graph = g;
+      e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+    } else if (g) {
+      cudaGraphDestroy(g);
+    }
+  }
+  cudaStreamDestroy(cs);
+  h->launches = launches0;               // captured, not yet launched
+  if (rc == XFLAT_OK && e != cudaSuccess) rc = fail(h, XFLAT_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  if (rc != XFLAT_OK) {
+    cudaGetLastError();
+    drop_graph(h);
+    return rc;
+  }
+  h->graph_launches = n_launches;
+  h->graph_steps = max_steps;
   return XFLAT_OK;
 }
 
@@ -746,6 +795,7 @@ int xflat_create_batch(const xflat_config* cfgs, uint32_t n_inst, xflat_t* out) 
 int xflat_destroy(xflat_t h) {
   if (!h) return XFLAT_OK;
   if (h->stream || true) cudaStreamSynchronize(h->stream);
+  drop_graph(h);
   void* ptrs[] = {h->planes, h->d_ic, h->d_dyn, h->d_pieces, h->d_blk, h->d_acc, h->d_errmax,
                   h->d_nonfinite, h->d_etab, h->d_u, h->d_du, h->d_bar, h->d_words, h->d_stage,
                   h->d_trace};
@@ -842,6 +892,20 @@ int xflat_advance(xflat_t h, const double* r1, uint32_t max_steps, int* done_out
   if (!h) return XFLAT_ERR_INVAL;
   if (max_steps == 0) return fail(h, XFLAT_ERR_INVAL, "max_steps must be >= 1");
   return do_evolve(h, r1, false, max_steps, done_out);
+}
+
+int xflat_advance_graph(xflat_t h, uint32_t n_launches, uint32_t max_steps, int* done_out) {
+  if (!h) return XFLAT_ERR_INVAL;
+  if (n_launches == 0 || max_steps == 0) return fail(h, XFLAT_ERR_INVAL, "n_launches and max_steps must be >= 1");
+  if (!(h->advancing && h->moments_valid))
+    return fail(h, XFLAT_ERR_STATE, "xflat_advance must precede xflat_advance_graph");
+  int rc;
+  if (!h->graph_exec || h->graph_launches != n_launches || h->graph_steps != max_steps)
+    if ((rc = capture_graph(h, n_launches, max_steps))) return rc;
+  if (done_out) *done_out = h->h_words[1];
+  CUDA_TRY(h, cudaGraphLaunch(h->graph_exec, h->stream));
+  h->launches += n_launches;
+  return XFLAT_OK;
 }
 
 int xflat_moments_inst(xflat_t h, uint32_t inst, double* J0, double* J1) {

@@ -67,6 +67,7 @@ _SIGS = {
     "xflat_evolve": (_H, C.c_double, C.c_double),
     "xflat_evolve_batch": (_H, _P),
     "xflat_advance": (_H, _P, C.c_uint32, C.POINTER(C.c_int)),
+    "xflat_advance_graph": (_H, C.c_uint32, C.c_uint32, C.POINTER(C.c_int)),
     "xflat_moments": (_H, _P, _P),
     "xflat_moments_inst": (_H, C.c_uint32, _P, _P),
     "xflat_get_rho": (_H, _P, C.c_int, C.c_int),
@@ -195,6 +196,11 @@ class Solver:
         done = C.c_int(0)
         r1p = None if r1 is None else np.ascontiguousarray(r1, dtype=np.float64)
         _check(_lib.xflat_advance(self.h, _ptr(r1p), max_steps, C.byref(done)), self.h)
+        return bool(done.value)
+
+    def advance_graph(self, n_launches, max_steps=1):
+        done = C.c_int(0)
+        _check(_lib.xflat_advance_graph(self.h, n_launches, max_steps, C.byref(done)), self.h)
         return bool(done.value)
 
     def moments(self, inst=0):
