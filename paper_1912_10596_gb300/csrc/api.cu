@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/xflat.h"
+#include "adjoint.cuh"
 #include "kernels.h"
 #include "xflat_internal.cuh"
 #include "step_kernel.cuh"
@@ -1068,8 +1069,152 @@ int xflat_get_stats_inst(xflat_t h, uint32_t inst, xflat_stats* out) {
 
 int xflat_get_stats(xflat_t h, xflat_stats* out) { return xflat_get_stats_inst(h, 0, out); }
 
-int xflat_adjoint(xflat_t h, double, double, uint32_t, uint32_t, double*, double*, double*) {
-  return fail(h, XFLAT_ERR_UNSUPPORTED, "adjoint not built");
+int xflat_adjoint(xflat_t h, double r0_km, double r1_km, uint32_t n_steps, uint32_t checkpoint_every,
+                  double* dJ_dN, double* dJ_dtheta, double* J_out) {
+  if (!h) return XFLAT_ERR_INVAL;
+  if (h->nf != 2 || h->inst.size() != 1)
+    return fail(h, XFLAT_ERR_UNSUPPORTED, "the adjoint is built for one two-flavour instance");
+  HostInst& I = h->inst[0];
+  if (!I.spectra) return fail(h, XFLAT_ERR_STATE, "set_spectra before the adjoint");
+  if (!is_fin(r0_km) || !is_fin(r1_km) || r0_km < I.cfg.R_km || !(r1_km > r0_km))
+    return fail(h, XFLAT_ERR_INVAL, "need R <= r0 < r1, finite");
+  if (n_steps == 0 || checkpoint_every == 0) return fail(h, XFLAT_ERR_INVAL, "n_steps and checkpoint_every must be >= 1");
+  const uint32_t ne = I.cfg.n_energy, na = I.cfg.n_angle, n = I.n_beams;
+  const uint32_t K = std::min(checkpoint_every, n_steps);
+  const uint32_t n_ck = (n_steps + K - 1) / K;
+  // host tables (the forward step kernel's tables, in double)
+  InstConst ic = h->ic[0];
+  std::vector<double> et;
+  build_tables(h, I, et, ic);
+  double SW = 0.0;
+  for (uint32_t j = 0; j < na; ++j)
+    for (uint32_t k = 0; k < ne; ++k) SW += I.du[j] * I.N[k];
+  if (!(SW > 0)) return fail(h, XFLAT_ERR_INVAL, "the objective needs a positive nu_e luminosity");
+  std::vector<double> objw(ne);
+  for (uint32_t k = 0; k < ne; ++k) objw[k] = I.N[k] / SW;
+  int G = adjoint_blocks_per_sm() * h->sm_count;
+  if (G < 1) return fail(h, XFLAT_ERR_CUDA, "adjoint kernel does not fit on an SM");
+  G = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)G, ((uint64_t)n + kAdjBlock - 1) / kAdjBlock));
+  // device buffers
+  const size_t n3 = 3ull * n;
+  const size_t words = ne + 2ull * ne + 2 * na + ne                // omega, g, u, du, objw
+                     + 3 * n3 + (size_t)n_ck * n3 + (size_t)K * n3 // y, ksum, klast, ck, seg
+                     + (size_t)K * 4 * kAdjStageVals + 3 * n3      // stage_sc, ystage
+                     + 3 * n3 + 2ull * n                           // a, ybar, v, gw, gth
+                     + (size_t)G * kAdjPartStride + kGlobWords     // part, glob
+                     + 5ull * ne;                                  // pee_sum, gw_sum, gth_sum
+  double* base = nullptr;
+  Barrier* bar = nullptr;
+  int* status = nullptr;
+  if (cudaMalloc(&base, words * sizeof(double)) != cudaSuccess) return fail(h, XFLAT_ERR_NOMEM, "adjoint buffers");
+  if (cudaMalloc(&bar, sizeof(Barrier)) != cudaSuccess || cudaMalloc(&status, sizeof(int)) != cudaSuccess) {
+    cudaFree(base);
+    if (bar) cudaFree(bar);
+    return fail(h, XFLAT_ERR_NOMEM, "adjoint barrier");
+  }
+  auto release_all = [&]() { cudaFree(base); cudaFree(bar); cudaFree(status); };
+  double* q = base;
+  auto take = [&](size_t cnt) { double* r = q; q += cnt; return r; };
+  AdjParams p{};
+  p.n_beams = n;
+  p.n_energy = ne;
+  p.n_angle = na;
+  double* d_omega = take(ne);
+  double* d_g = take(2ull * ne);
+  double* d_u = take(na);
+  double* d_du = take(na);
+  double* d_objw = take(ne);
+  p.omega = d_omega; p.g = d_g; p.u = d_u; p.du = d_du; p.objw = d_objw;
+  p.ic = ic;
+  p.r0 = r0_km;
+  p.h = (r1_km - r0_km) / (double)n_steps;
+  p.n_steps = (int)n_steps;
+  p.ck_every = (int)K;
+  p.y = take(n3); p.ksum = take(n3); p.klast = take(n3);
+  p.ck = take((size_t)n_ck * n3);
+  p.seg = take((size_t)K * n3);
+  p.stage_sc = take((size_t)K * 4 * kAdjStageVals);
+  p.ystage = take(3 * n3);
+  p.a = take(n3); p.ybar = take(n3); p.v = take(n3);
+  p.gw = take(n); p.gth = take(n);
+  p.part = take((size_t)G * kAdjPartStride);
+  p.glob = take(kGlobWords);
+  double* d_pee = take(ne);
+  double* d_gws = take(2ull * ne);
+  double* d_gths = take(2ull * ne);
+  p.bar = bar;
+  p.timeout_ns = h->timeout_ns;
+  p.status = status;
+  cudaStream_t st = h->stream;
+  int rc = XFLAT_OK;
+  auto check = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && rc == XFLAT_OK) rc = fail(h, XFLAT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return rc == XFLAT_OK;
+  };
+  auto device_status = [&]() {
+    int s = 0;
+    if (!check(cudaMemcpyAsync(&s, status, sizeof(int), cudaMemcpyDeviceToHost, st), "status read")) return false;
+    if (!check(cudaStreamSynchronize(st), "adjoint launch")) return false;
+    if (s) rc = fail(h, s, std::string("adjoint device status: ") + xflat_status_string(s));
+    return rc == XFLAT_OK;
+  };
+  // the initial condition of Sec. 3.4: s = z (P = diag(1, 0)) for every beam
+  std::vector<double> y0(n3, 0.0);
+  for (uint32_t b = 0; b < n; ++b) y0[2ull * n + b] = 1.0;
+  std::vector<double> pee(ne), gws(2ull * ne), gths(2ull * ne);
+  double J = 0.0;
+  check(cudaMemcpyAsync(d_omega, et.data(), ne * 8, cudaMemcpyHostToDevice, st), "upload") &&
+  check(cudaMemcpyAsync(d_g, et.data() + ne, 2ull * ne * 8, cudaMemcpyHostToDevice, st), "upload") &&
+  check(cudaMemcpyAsync(d_u, I.u.data(), na * 8, cudaMemcpyHostToDevice, st), "upload") &&
+  check(cudaMemcpyAsync(d_du, I.du.data(), na * 8, cudaMemcpyHostToDevice, st), "upload") &&
+  check(cudaMemcpyAsync(d_objw, objw.data(), ne * 8, cudaMemcpyHostToDevice, st), "upload") &&
+  check(cudaMemcpyAsync(p.y, y0.data(), n3 * 8, cudaMemcpyHostToDevice, st), "upload") &&
+  check(cudaMemsetAsync(bar, 0, sizeof(Barrier), st), "memset") &&
+  check(cudaMemsetAsync(status, 0, sizeof(int), st), "memset") &&
+  check(cudaMemsetAsync(p.klast, 0, n3 * 8, st), "memset");
+  if (rc == XFLAT_OK) {
+    p.mode = kAdjForward;
+    if (check(adjoint_launch(p, G, st), "adjoint forward launch") && device_status()) {
+      check(adjoint_energy_sums(p, d_pee, d_gws, d_gths, st), "energy sums");
+      check(cudaMemcpyAsync(pee.data(), d_pee, ne * 8, cudaMemcpyDeviceToHost, st), "download");
+      check(cudaMemcpyAsync(&J, p.glob + kGlobJ, 8, cudaMemcpyDeviceToHost, st), "download");
+    }
+  }
+  for (int c = (int)n_ck - 1; c >= 0 && rc == XFLAT_OK; --c) {
+    p.mode = kAdjBackward;
+    p.seg_first = c * (int)K;
+    p.seg_count = std::min<int>((int)K, (int)n_steps - c * (int)K);
+    if (!check(adjoint_launch(p, G, st), "adjoint backward launch")) break;
+    if (c == 0 || (c % 16) == 0) device_status();
+  }
+  if (rc == XFLAT_OK) {
+    check(adjoint_energy_sums(p, d_pee, d_gws, d_gths, st), "energy sums");
+    check(cudaMemcpyAsync(gws.data(), d_gws, 2ull * ne * 8, cudaMemcpyDeviceToHost, st), "download");
+    check(cudaMemcpyAsync(gths.data(), d_gths, 2ull * ne * 8, cudaMemcpyDeviceToHost, st), "download");
+    check(cudaStreamSynchronize(st), "adjoint");
+  }
+  release_all();
+  if (rc != XFLAT_OK) return rc;
+  // chain rule to the per-bin luminosities: g_nu,k = (N_e - N_x)/ws, g_nubar,k = -(Nbar_e - Nbar_x)/ws
+  // (mu carries ws, so J depends on N only through the products mu g), plus the objective's own
+  // weights du_j N_e,k
+  const double ws = ic.wscale;
+  if (dJ_dN) {
+    for (uint32_t k = 0; k < ne; ++k) {
+      const double gn = gws[k] / ws, gb = gws[ne + k] / ws;
+      dJ_dN[0 * ne + k] = gn + pee[k] / SW;                // N[nu][e][k]
+      dJ_dN[1 * ne + k] = -gn;                             // N[nu][x][k]
+      dJ_dN[2 * ne + k] = -gb;                             // N[nubar][e][k]
+      dJ_dN[3 * ne + k] = gb;                              // N[nubar][x][k]
+    }
+  }
+  if (dJ_dtheta) {
+    double t = 0.0;
+    for (size_t i = 0; i < gths.size(); ++i) t += gths[i];
+    *dJ_dtheta = t;
+  }
+  if (J_out) *J_out = J;
+  return XFLAT_OK;
 }
 
 const char* xflat_status_string(int s) {
