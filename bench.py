@@ -30,6 +30,22 @@ from bulb_inputs import workload_2f_large  # noqa: E402
 BYTES_PER_BEAM_STAGE = {("mixed", "dp45"): 14.0, ("fp64", "dp45"): 28.0,
                         ("mixed", "rk4"): 15.0, ("fp64", "rk4"): 30.0}
 L2_BYTES = 129 * 1024 * 1024
+# DRAM traffic of one step launch of the timed kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture, profiles/step_kernel_mixed_dp45_4M.md).  It holds only
+# for the kernel sources it was taken on, identified by their SHA-256; after any change to them the
+# benchmark reports null until a new capture is recorded here.
+STEP_TRAFFIC = {"bytes": 55.03e6,
+                "sources_sha256": "7f5a6a22d6af2305af8c3525b30206c3b5a4f5c5d211c23e9eb5e0c27be37fd1"}
+KERNEL_SOURCES = ["step_kernel.cuh", "xflat_internal.cuh", "kernels_2f.cu"]
+
+
+def step_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1912_10596_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return STEP_TRAFFIC["bytes"] if h.hexdigest() == STEP_TRAFFIC["sources_sha256"] else None
 METRIC = "beam-updates/s (beams x RK stages)"
 
 
@@ -225,6 +241,7 @@ def main():
     import __graft_entry__ as g
     g.build()
     from paper_1912_10596_gb300 import xflat as xf
+    from paper_1912_10596_gb300 import shard
 
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     flush = lambda: flush_l2(flush_buf)  # noqa: E731
@@ -240,11 +257,7 @@ def main():
     with ClockSampler(torch.cuda.current_device()) as clk:
         ms, bsu, st, solver = time_device_steps(xf, torch, wl, "mixed", args.steps, args.warmup, flush, shape)
     clocks = clk.summary()
-    t_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([t_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = shard.max_over_ranks(sum(ms))                      # the slowest rank's time
     value = world * bsu * args.steps / (t_ms / 1e3)
     hbm, peak_kind = _peaks()
     per_launch_ms = statistics.mean(ms)
@@ -280,7 +293,7 @@ def main():
                        "grid_blocks": st.grid_blocks, "block_size": st.block_size,
                        "autotuned_shape": list(shape) if shape else None},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm, "traffic": step_traffic(),
                          "note": f"{BYTES_PER_BEAM_STAGE[('mixed', 'dp45')]} algorithmic B per beam-stage; peak {peak_kind}"},
             "clocks": clocks,
             "gpu_launches": args.steps,

@@ -349,11 +349,18 @@ struct KParams {
   int trace_passes;
 };
 
+// Add x (|x| < 2^63) to a 128-bit fixed-point accumulator (acc2[0]: fraction in units of 2^-64,
+// acc2[1]: signed integer part), truncating |x| below 2^-64.  The split is done on |x|, where
+// |x| - floor(|x|) is exact, and the pair is negated as a 128-bit integer for x < 0 (x - floor(x)
+// itself would round for small negative x).
 __device__ __forceinline__ void fx_add(unsigned long long* acc2, double x) {
-  const double hi_d = floor(x);
-  const double frac = x - hi_d;                                   // exact, in [0, 1)
-  const unsigned long long lo = (unsigned long long)(frac * 18446744073709551616.0);
-  const long long hi = (long long)hi_d;
+  const double ax = fabs(x);
+  const double hi_d = floor(ax);
+  const unsigned long long lo_a = (unsigned long long)((ax - hi_d) * 18446744073709551616.0);
+  const long long hi_a = (long long)hi_d;
+  const bool neg = x < 0.0;
+  const unsigned long long lo = neg ? 0ull - lo_a : lo_a;
+  const long long hi = neg ? -hi_a - (lo_a != 0ull ? 1ll : 0ll) : hi_a;
   const unsigned long long old = atomicAdd(&acc2[0], lo);
   const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
   atomicAdd(&acc2[1], (unsigned long long)hi + carry);

@@ -12,7 +12,7 @@ import pytest
 from scipy.integrate import solve_ivp
 from scipy.linalg import expm
 
-from bulb_inputs import Workload, number_luminosity_bins
+from bulb_inputs import Workload, number_luminosity_bins, workload_2f_small_fp64
 from oracle import physics as ph
 from oracle import four_psi
 from oracle.expm import two_flavor_propagator, hermitian_propagator
@@ -375,3 +375,22 @@ def test_spectra_normalisation():
     assert abs(N[0, 0].sum() / (1e51 / (11 * MeV)) - 1) < 1e-13
     assert abs(N[1, 0].sum() / (2e51 / (16 * MeV)) - 1) < 1e-13
     assert abs(N[1, 1].sum() / (3e51 / (25 * MeV)) - 1) < 1e-13
+
+
+def test_order_sensitivity_floor():
+    """How much the FP64 result depends on the order of the sums over beams: the small workload
+    over its parity window (2000 RK4 steps, 100 -> 200 km) with the angle and energy bins in
+    reverse order (so every moment sum runs backwards), mapped back, against the plain order.
+    The FP64 parity gate is max(1e-10, 10 x floor); the floor must sit well below it."""
+    wl = workload_2f_small_fp64()
+    g = Grid.from_workload(wl)
+    rev = Grid(E=g.E[::-1].copy(), u=g.u[::-1].copy(), du=g.du[::-1].copy(), N=g.N[:, :, ::-1].copy())
+    outs = []
+    for grid in (g, rev):
+        b = Bulb(wl, grid=grid)
+        Y, _ = evolve_fixed(b, b.initial_state(), 100.0, 200.0, 2000)
+        outs.append(Y)
+    A, B = outs[0], outs[1][:, ::-1, ::-1]
+    floor = float((np.sqrt((np.abs(A - B) ** 2).sum(axis=(-2, -1)))
+                   / np.sqrt((np.abs(A) ** 2).sum(axis=(-2, -1)))).max())
+    assert 0.0 < floor < 1e-11, floor
