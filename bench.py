@@ -117,8 +117,19 @@ def bench_config(xf, wl, precision):
                                    atol=1e-6 if precision == "mixed" else 1e-9)
 
 
-def time_device_steps(xf, torch, wl, precision, steps, warmup, flush, shape=None):
-    """Return (ms per step, beam-stage updates per step, stats) for `steps` timed single-step launches."""
+def launch_chunks(steps, per_launch):
+    """Split `steps` radial steps into persistent launches of at most `per_launch` steps."""
+    out = []
+    while steps > 0:
+        out.append(min(per_launch, steps))
+        steps -= out[-1]
+    return out
+
+
+def time_device_steps(xf, torch, wl, precision, steps, warmup, flush, shape=None, per_launch=1):
+    """Time exactly `steps` radial steps, run as persistent launches of up to `per_launch` steps
+    with the L2 flushed before every launch.  Returns (ms per launch, launch sizes, beam-stage
+    updates per step, stats, solver)."""
     stream = torch.cuda.current_stream()
     cfg = bench_config(xf, wl, precision)
     if shape is not None:
@@ -131,10 +142,11 @@ def time_device_steps(xf, torch, wl, precision, steps, warmup, flush, shape=None
         s.advance(None, max_steps=1)
     torch.cuda.synchronize()
     st0 = s.stats()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for e0, e1 in evs:
+    chunks = launch_chunks(steps, per_launch)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in chunks]
+    for (e0, e1), n in zip(evs, chunks):
         flush(); e0.record(stream)
-        s.advance(None, max_steps=1)
+        s.advance(None, max_steps=n)
         e1.record(stream)
     torch.cuda.synchronize()
     st1 = s.stats()
@@ -142,7 +154,7 @@ def time_device_steps(xf, torch, wl, precision, steps, warmup, flush, shape=None
     if st1.status != 0:
         raise RuntimeError(f"device status {st1.status}")
     bsu = (st1.beam_stage_updates - st0.beam_stage_updates) / steps
-    return ms, bsu, st1, s
+    return ms, chunks, bsu, st1, s
 
 
 def e2e_steps(xf, torch, s, wl, steps):
@@ -203,6 +215,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--steps-per-launch", type=int, default=8,
+                    help="radial steps per persistent launch in the timed region (L2 flushed before each)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -254,21 +268,25 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    spl = max(1, args.steps_per_launch)
     with ClockSampler(torch.cuda.current_device()) as clk:
-        ms, bsu, st, solver = time_device_steps(xf, torch, wl, "mixed", args.steps, args.warmup, flush, shape)
+        ms, chunks, bsu, st, solver = time_device_steps(xf, torch, wl, "mixed", args.steps, args.warmup,
+                                                        flush, shape, spl)
     clocks = clk.summary()
     t_ms = shard.max_over_ranks(sum(ms))                      # the slowest rank's time
     value = world * bsu * args.steps / (t_ms / 1e3)
     hbm, peak_kind = _peaks()
-    per_launch_ms = statistics.mean(ms)
-    achieved = BYTES_PER_BEAM_STAGE[("mixed", "dp45")] * bsu / (per_launch_ms / 1e3) / 1e9
+    # algorithmic bytes of all timed launches over their summed CUDA-event durations (= per launch
+    # bytes over the mean launch duration when the launches are equal)
+    achieved = BYTES_PER_BEAM_STAGE[("mixed", "dp45")] * bsu * args.steps / (sum(ms) / 1e3) / 1e9
 
     fp64 = None
     if not args.no_fp64:
         k64 = max(3, args.steps // 4)
-        ms64, bsu64, st64, s64 = time_device_steps(xf, torch, wl, "fp64", k64, args.warmup, flush)
+        ms64, _, bsu64, st64, s64 = time_device_steps(xf, torch, wl, "fp64", k64, args.warmup, flush,
+                                                      None, spl)
         v64 = bsu64 * k64 / (sum(ms64) / 1e3)
-        fp64 = {"value": v64, "unit": "beam-updates/s", "ms_per_step": statistics.mean(ms64),
+        fp64 = {"value": v64, "unit": "beam-updates/s", "ms_per_step": sum(ms64) / k64,
                 "speedup_mixed_vs_fp64": (bsu * args.steps / (sum(ms) / 1e3)) / v64}
         del s64
     e2e = None
@@ -289,14 +307,15 @@ def main():
             "dtype": "f32 per-beam + f64 reductions", "data": "synthetic",
             "config": {"workload": wl.name, "beams": wl.n_beams, "integrator": "dp45",
                        "precision": "mixed", "r_start_km": 11.0, "stage_evals_per_step": bsu / wl.n_beams,
-                       "l2": "flushed between timed steps (write of a 258 MB buffer)",
+                       "steps_per_launch": spl,
+                       "l2": f"flushed before every timed launch of up to {spl} steps (write of a 258 MB buffer)",
                        "grid_blocks": st.grid_blocks, "block_size": st.block_size,
                        "autotuned_shape": list(shape) if shape else None},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": step_traffic(),
                          "note": f"{BYTES_PER_BEAM_STAGE[('mixed', 'dp45')]} algorithmic B per beam-stage; peak {peak_kind}"},
             "clocks": clocks,
-            "gpu_launches": args.steps,
+            "gpu_launches": len(chunks),
             "fp64_path": fp64,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -52,6 +52,7 @@ struct xflat_s {
   int device = 0, sm_count = 0;
   // device memory
   void* planes = nullptr;                  // [2][nc][stride] Real
+  void* escr = nullptr;                    // DP45: error partial + scale planes [nc + 1][stride] Real
   uint64_t stride = 0;
   InstConst* d_ic = nullptr;
   InstDyn* d_dyn = nullptr;
@@ -423,6 +424,7 @@ KParams make_params(xflat_t h, int n_steps, int init_only) {
   p.nonfinite = h->d_nonfinite;
   p.planeA = h->planes;
   p.planeB = (char*)h->planes + (size_t)h->nc * h->stride * h->real_size;
+  p.escr = h->escr;
   p.plane_stride = h->stride;
   p.etab = h->d_etab;
   p.u_tab = h->d_u;
@@ -722,6 +724,10 @@ int create_impl(const xflat_config* cfgs, uint32_t n, xflat_t* out) {
   h->stride = (off + 63) / 64 * 64;
   const size_t plane_bytes = 2ull * h->nc * h->stride * h->real_size;
   if (cudaMalloc(&h->planes, plane_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
+  // FP64 DP45: error partial (nc planes) and error scale (one plane) of the step in flight
+  if (h->integrator == XFLAT_DP45 && h->real_size == 8 &&
+      cudaMalloc(&h->escr, (size_t)(h->nc + 1) * h->stride * h->real_size) != cudaSuccess)
+    return bail(XFLAT_ERR_NOMEM);
   if (cudaMalloc(&h->d_ic, sizeof(InstConst) * n) != cudaSuccess ||
       cudaMalloc(&h->d_dyn, sizeof(InstDyn) * n) != cudaSuccess ||
       cudaMalloc(&h->d_acc, sizeof(unsigned long long) * n * kAccWordsPerInst) != cudaSuccess ||
@@ -797,7 +803,7 @@ int xflat_destroy(xflat_t h) {
   if (!h) return XFLAT_OK;
   if (h->stream || true) cudaStreamSynchronize(h->stream);
   drop_graph(h);
-  void* ptrs[] = {h->planes, h->d_ic, h->d_dyn, h->d_pieces, h->d_blk, h->d_acc, h->d_errmax,
+  void* ptrs[] = {h->planes, h->escr, h->d_ic, h->d_dyn, h->d_pieces, h->d_blk, h->d_acc, h->d_errmax,
                   h->d_nonfinite, h->d_etab, h->d_u, h->d_du, h->d_bar, h->d_words, h->d_stage,
                   h->d_trace};
   for (void* p : ptrs)

@@ -331,6 +331,7 @@ struct KParams {
   int* nonfinite;                // [n_inst]
   void* planeA;
   void* planeB;
+  void* escr;                    // adaptive tableaus: error partial and scale planes [NC + 1][plane_stride]
   uint64_t plane_stride;         // elements between component planes
   const void* etab;              // energy tables, Real, per instance at e_off: [n_tab][n_energy]
   const double* u_tab;           // angle positions u_j, at a_off
@@ -684,6 +685,14 @@ struct TabView {
 // What a pass does (compile time).
 enum PassKind : int { kStagePass = 0, kFinalPass = 1, kInitPass = 2 };
 
+// Adaptive FP64 kernels split the last two passes of a step: the pass forming Y_S (= y5, first
+// same as last) also stores y5, the error partial sum over stages 1..S-1 and the error scale, and
+// the final pass only adds k_S -- the stage chain costs FP64 instructions on GB300's narrow FP64
+// pipe.  FP32 kernels rebuild the chain in the final pass instead: their state, y5 and those
+// partials together exceed the L2, and the extra DRAM traffic costs more than the FP32 chain.
+template <class Tab, typename Real>
+__host__ __device__ constexpr bool split_final() { return Tab::kAdaptive && sizeof(Real) == 8; }
+
 template <class Phys, class Tab, typename Real, bool kCF, int kPass, int kKind>
 struct PassBody;
 
@@ -691,12 +700,20 @@ struct PassBody;
 template <class Phys, class Tab, typename Real, int kPass, int kKind>
 struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
   static constexpr int NC = Phys::NC;
-  // number of stage derivatives to rebuild before the stage state of this pass
+  static constexpr bool kSplit = split_final<Tab, Real>();
+  // number of stage derivatives to rebuild before the stage state of this pass (split final pass:
+  // none, the pass forming Y_S left y5 and the error partial behind; unsplit adaptive: S - 1, k_S
+  // follows from the new state)
   static constexpr int kChain =
-      kKind == kInitPass ? 0 : (kKind == kFinalPass ? Tab::S - (Tab::kAdaptive ? 1 : 0) : kPass + 1);
+      kKind == kInitPass ? 0
+      : (kKind == kFinalPass ? (kSplit ? 0 : Tab::S - (Tab::kAdaptive ? 1 : 0)) : kPass + 1);
+  // y: the step's state.  Split final pass: the pass forming Y_S replaces y by the new state
+  // y5 = Y_S and sets ep = (error partial sum over stages 1..S-1, atol + rtol max(|y|, |y5|)); the
+  // final pass gets y5 in y and that ep back.
   template <class BS>
   __device__ static inline void beam(const BS& bs, const typename Phys::Beam& bm,
                                      const TabView<Real, Phys>& tv, int tj, Real (&y)[NC],
+                                     Real (&ep)[NC + 1],
                                      Real (&acc)[Phys::NM], Real& emax, int& bad, bool mixed) {
     Real k[Tab::S + 1][NC];
 #pragma unroll
@@ -729,23 +746,43 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
           if (Tab::a(I, m) != 0.0) v += bs.hA[I][m] * k[m][i];
         Y[i] = v;
       }
+      if (kSplit && I == Tab::S) {
+        // first same as last: Y_S is the new state y5 (row S of A is b).  Its error partial sum
+        // over stages 1..S-1 and the error scale go with it, so the final pass needs only k_S.
+        if (!(Phys::tnorm2(y) <= rbig<Real>())) bad = 1;   // non-finite input state: fatal
+        if (mixed) Phys::normalise(Y);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+          Real v = 0;
+#pragma unroll
+          for (int m = 1; m < Tab::S; ++m)
+            if (Tab::e(m) != 0.0) v += bs.hE[m] * k[m][i];
+          ep[i] = v;
+        }
+        ep[NC] = bs.atol + bs.rtol * sqrt(fmax(Phys::tnorm2(y), Phys::tnorm2(Y)));
+        Phys::accum(acc, bm.w, Phys::t1(tv.row(I, tj)), Y);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) y[i] = Y[i];
+        return;
+      }
       if (Tab::kAdaptive && I == Tab::S && mixed) Phys::normalise(Y);
       Phys::accum(acc, bm.w, Phys::t1(tv.row(I, tj)), Y);
       return;
     }
-    // final pass
-    Real yn[NC];
+    if (Tab::kAdaptive && !kSplit) {
+      // final pass: y5 from the rebuilt chain, k_S = f(y5), the embedded error and the squared
+      // error ratio (its square root is taken once per block)
+      Real yn[NC];
 #pragma unroll
-    for (int i = 0; i < NC; ++i) {
-      Real v = y[i];
+      for (int i = 0; i < NC; ++i) {
+        Real v = y[i];
 #pragma unroll
-      for (int m = 1; m <= kChain; ++m)
-        if (Tab::b(m) != 0.0) v += bs.hB[m] * k[m][i];
-      yn[i] = v;
-    }
-    const bool ynok = Phys::tnorm2(yn) <= rbig<Real>();
-    if (mixed && ynok) Phys::normalise(yn);
-    if (Tab::kAdaptive) {
+        for (int m = 1; m <= kChain; ++m)
+          if (Tab::b(m) != 0.0) v += bs.hB[m] * k[m][i];
+        yn[i] = v;
+      }
+      const bool ynok = Phys::tnorm2(yn) <= rbig<Real>();
+      if (mixed && ynok) Phys::normalise(yn);
       if (!(Phys::tnorm2(y) <= rbig<Real>())) bad = 1;     // non-finite input state: fatal
       Real Kv[NC];
       Phys::K(tv.row(Tab::S, tj), bm, bs.vac, bs.scr[Tab::S], Kv);
@@ -759,15 +796,47 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
           if (Tab::e(m) != 0.0) v += bs.hE[m] * k[m][i];
         e[i] = v;
       }
-      const Real en = Phys::enorm(e);
-      const Real sn = sqrt(fmax(Phys::tnorm2(y), Phys::tnorm2(yn)));
-      Real ratio = en / (bs.atol + bs.rtol * sn);
-      // a trial step whose stages overflowed the working precision is rejected, not fatal
-      if (!(ratio <= rbig<Real>()) || !ynok) ratio = Real(INFINITY);
-      emax = fmax(emax, ratio);
-    } else {
-      Phys::accum(acc, bm.w, Phys::t1(tv.row(Tab::S, tj)), yn);
+      const Real den = bs.atol + bs.rtol * sqrt(fmax(Phys::tnorm2(y), Phys::tnorm2(yn)));
+      Real r2 = Phys::tnorm2(e) / (den * den);
+      if (!(r2 <= rbig<Real>()) || !ynok) r2 = Real(INFINITY);
+      emax = fmax(emax, r2);
+#pragma unroll
+      for (int i = 0; i < NC; ++i) y[i] = yn[i];
+      return;
     }
+    if (Tab::kAdaptive) {
+      // split final pass (y holds y5): k_S = f(y5) with the moments of y5, the embedded error,
+      // and the squared error ratio (its square root is taken once per block)
+      const bool ynok = Phys::tnorm2(y) <= rbig<Real>();
+      Real Kv[NC], kS[NC], e[NC];
+      Phys::K(tv.row(Tab::S, tj), bm, bs.vac, bs.scr[Tab::S], Kv);
+      Phys::f(Kv, y, kS);
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        Real v = ep[i];
+        v += bs.hE[Tab::S] * kS[i];
+        e[i] = v;
+      }
+      const Real den = ep[NC];
+      Real r2 = Phys::tnorm2(e) / (den * den);
+      // a trial step whose stages overflowed the working precision is rejected, not fatal
+      if (!(r2 <= rbig<Real>()) || !ynok) r2 = Real(INFINITY);
+      emax = fmax(emax, r2);
+      return;
+    }
+    // final pass of a fixed-step tableau
+    Real yn[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      Real v = y[i];
+#pragma unroll
+      for (int m = 1; m <= kChain; ++m)
+        if (Tab::b(m) != 0.0) v += bs.hB[m] * k[m][i];
+      yn[i] = v;
+    }
+    const bool ynok = Phys::tnorm2(yn) <= rbig<Real>();
+    if (mixed && ynok) Phys::normalise(yn);
+    Phys::accum(acc, bm.w, Phys::t1(tv.row(Tab::S, tj)), yn);
 #pragma unroll
     for (int i = 0; i < NC; ++i) y[i] = yn[i];
   }
@@ -780,6 +849,7 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
   template <class BS>
   __device__ static inline void beam(const BS& bs, const typename Phys::Beam& bm,
                                      const TabView<Real, Phys>& tv, int tj, Real (&y)[NC],
+                                     Real (&)[NC + 1],
                                      Real (&acc)[Phys::NM], Real& emax, int& bad, bool mixed) {
     if (kKind == kInitPass) {
       Phys::accum(acc, bm.w, Phys::t1(tv.row(1, tj)), y);
@@ -858,6 +928,7 @@ __device__ __forceinline__ F2 mul2(F2 a, F2 b) {
 template <class Tab, int kPass, int kKind>
 struct PairRK {
   using P = Phys2<float>;
+  static_assert(!split_final<Tab, float>(), "FP32 passes rebuild the chain in the final pass");
   static constexpr int kChain =
       kKind == kInitPass ? 0 : (kKind == kFinalPass ? Tab::S - (Tab::kAdaptive ? 1 : 0) : kPass + 1);
 
@@ -892,10 +963,11 @@ struct PairRK {
     for (int i = 0; i < 3; ++i) y[i] = mul2(y[i], inv);
   }
 
-  // rows: table rows of this pair's angle bin, stage s at rows + s * rstride (in F2 units)
+  // rows: table rows of this pair's angle bin, stage s at rows + s * rstride (in F2 units);
+  // y, ep as in PassBody::beam
   template <class BS>
   __device__ static inline void run(const BS& bs, F2 eo, F2 w, const F2* rows, int rstride, F2 (&y)[3],
-                                    F2 (&acc)[6], float& emax, int& bad) {
+                                    F2 (&ep)[4], F2 (&acc)[6], float& emax, int& bad) {
     F2 k[Tab::S + 1][3];
 #pragma unroll
     for (int l = 1; l <= kChain; ++l) {
@@ -929,7 +1001,67 @@ struct PairRK {
       accum(acc, w, rows[rstride * I + P::vT1], Y);
       return;
     }
-    // final pass
+    if (Tab::kAdaptive) {
+      // final pass: y5 from the rebuilt chain, k_S = f(y5), the embedded error and the squared
+      // error ratio |e|_F^2 / scale^2 (its square root is taken once per block)
+      F2 yn[3] = {y[0], y[1], y[2]};
+#pragma unroll
+      for (int m = 1; m <= kChain; ++m)
+        if (Tab::b(m) != 0.0) {
+          const F2 hb = bs.hB2[m];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) yn[i] = fma2(hb, k[m][i], yn[i]);
+        }
+      F2 n2y = mul2(y[0], y[0]);
+      n2y = fma2(y[1], y[1], n2y);
+      n2y = fma2(y[2], y[2], n2y);
+      F2 n2n = mul2(yn[0], yn[0]);
+      n2n = fma2(yn[1], yn[1], n2n);
+      n2n = fma2(yn[2], yn[2], n2n);
+      float a0, a1, c0, c1;
+      upk(n2y, a0, a1);
+      upk(n2n, c0, c1);
+      if (!(a0 <= 3.0e38f) || !(a1 <= 3.0e38f)) bad = 1;    // non-finite input state: fatal
+      const bool ok0 = c0 <= 3.0e38f, ok1 = c1 <= 3.0e38f;
+      if (ok0 && ok1) {
+        const F2 inv = pk(1.0f / sqrtf(c0), 1.0f / sqrtf(c1));
+#pragma unroll
+        for (int i = 0; i < 3; ++i) yn[i] = mul2(yn[i], inv);
+      }
+      F2 K[3], nK[3];
+      Kpair(rows + Tab::S * rstride, eo, K, nK);
+      cross(K, nK, yn, k[Tab::S]);
+      F2 e[3] = {0ull, 0ull, 0ull};
+#pragma unroll
+      for (int m = 1; m <= Tab::S; ++m)
+        if (Tab::e(m) != 0.0) {
+          const F2 he = bs.hE2[m];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) e[i] = fma2(he, k[m][i], e[i]);
+        }
+      F2 e2 = mul2(e[0], e[0]);
+      e2 = fma2(e[1], e[1], e2);
+      e2 = fma2(e[2], e[2], e2);
+      F2 m2 = mul2(yn[0], yn[0]);
+      m2 = fma2(yn[1], yn[1], m2);
+      m2 = fma2(yn[2], yn[2], m2);
+      float e20, e21, m20, m21;
+      upk(e2, e20, e21);
+      upk(m2, m20, m21);
+      // |P~|_F = |s| / sqrt(2), |e|_F^2 = |e|^2 / 2
+      const float atol = bs.atol, rtol = bs.rtol;
+      const float s0 = atol + rtol * sqrtf(0.5f * fmaxf(a0, m20));
+      const float s1 = atol + rtol * sqrtf(0.5f * fmaxf(a1, m21));
+      float r0 = __fdiv_rn(0.5f * e20, s0 * s0);
+      float r1 = __fdiv_rn(0.5f * e21, s1 * s1);
+      if (!(r0 <= 3.0e38f) || !ok0) r0 = INFINITY;
+      if (!(r1 <= 3.0e38f) || !ok1) r1 = INFINITY;
+      emax = fmaxf(emax, fmaxf(r0, r1));
+#pragma unroll
+      for (int i = 0; i < 3; ++i) y[i] = yn[i];
+      return;
+    }
+    // final pass of a fixed-step tableau
     F2 yn[3] = {y[0], y[1], y[2]};
 #pragma unroll
     for (int m = 1; m <= kChain; ++m)
@@ -944,34 +1076,7 @@ struct PairRK {
     const bool ok0 = 0.5f * (a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]) <= 3.0e38f;
     const bool ok1 = 0.5f * (a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]) <= 3.0e38f;
     if (ok0 && ok1) normalise(yn);
-    if (Tab::kAdaptive) {
-      float y0[3], y1[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) upk(y[i], y0[i], y1[i]);
-      if (!(P::tnorm2(y0) <= 3.0e38f) || !(P::tnorm2(y1) <= 3.0e38f)) bad = 1;
-      F2 K[3], nK[3];
-      Kpair(rows + Tab::S * rstride, eo, K, nK);
-      cross(K, nK, yn, k[Tab::S]);
-      F2 e[3] = {0ull, 0ull, 0ull};
-#pragma unroll
-      for (int m = 1; m <= Tab::S; ++m)
-        if (Tab::e(m) != 0.0) {
-          const F2 he = bs.hE2[m];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) e[i] = fma2(he, k[m][i], e[i]);
-        }
-      float e0[3], e1[3], n0[3], n1[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) { upk(e[i], e0[i], e1[i]); upk(yn[i], n0[i], n1[i]); }
-      const float atol = bs.atol, rtol = bs.rtol;
-      float r0 = P::enorm(e0) / (atol + rtol * sqrtf(fmaxf(P::tnorm2(y0), P::tnorm2(n0))));
-      float r1 = P::enorm(e1) / (atol + rtol * sqrtf(fmaxf(P::tnorm2(y1), P::tnorm2(n1))));
-      if (!(r0 <= 3.0e38f) || !ok0) r0 = INFINITY;
-      if (!(r1 <= 3.0e38f) || !ok1) r1 = INFINITY;
-      emax = fmaxf(emax, fmaxf(r0, r1));
-    } else {
-      accum(acc, w, rows[rstride * Tab::S + P::vT1], yn);
-    }
+    accum(acc, w, rows[rstride * Tab::S + P::vT1], yn);
 #pragma unroll
     for (int i = 0; i < 3; ++i) y[i] = yn[i];
   }
@@ -1105,6 +1210,12 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     const Real* et = reinterpret_cast<const Real*>(p.etab) + ic.e_off;
     const Real* yin = reinterpret_cast<const Real*>(bs.parity ? p.planeB : p.planeA) + ic.beam_off;
     Real* yout = reinterpret_cast<Real*>(bs.parity ? p.planeA : p.planeB) + ic.beam_off;
+    // split final pass (see split_final): the pass forming Y_S stores y5 (into the output planes),
+    // the error partial and the error scale; the final pass reads those instead of the chain
+    constexpr bool kSplitStore = split_final<Tab, Real>() && kKind == kStagePass && kPass + 2 == Tab::S;
+    constexpr bool kSplitLoad = split_final<Tab, Real>() && kKind == kFinalPass;
+    Real* escr = reinterpret_cast<Real*>(p.escr) + ic.beam_off;
+    const Real* ysrc = kSplitLoad ? yout : yin;
     const int ne = (int)ic.n_energy, na = (int)ic.n_angle;
     Real acc[NM];
 #pragma unroll
@@ -1123,7 +1234,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     Real nxt[NC][VN];
     if (kPrefetch && pc.start + VN * threadIdx.x < end) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) vload(yin + (size_t)c * p.plane_stride + pc.start + VN * threadIdx.x, nxt[c]);
+      for (int c = 0; c < NC; ++c) vload(ysrc + (size_t)c * p.plane_stride + pc.start + VN * threadIdx.x, nxt[c]);
     }
     for (uint32_t l0 = pc.start + VN * threadIdx.x; l0 < end; l0 += vstep) {
       Real ys[NC][VN];
@@ -1134,11 +1245,16 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
           for (int v = 0; v < VN; ++v) ys[c][v] = nxt[c][v];
         if (l0 + vstep < end) {
 #pragma unroll
-          for (int c = 0; c < NC; ++c) vload(yin + (size_t)c * p.plane_stride + l0 + vstep, nxt[c]);
+          for (int c = 0; c < NC; ++c) vload(ysrc + (size_t)c * p.plane_stride + l0 + vstep, nxt[c]);
         }
       } else {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) vload(yin + (size_t)c * p.plane_stride + l0, ys[c]);
+        for (int c = 0; c < NC; ++c) vload(ysrc + (size_t)c * p.plane_stride + l0, ys[c]);
+      }
+      Real ep[NC + 1][VN];
+      if constexpr (kSplitLoad) {
+#pragma unroll
+        for (int c = 0; c <= NC; ++c) vload(escr + (size_t)c * p.plane_stride + l0, ep[c]);
       }
       int jj = (int)fast_div(l0, ic.div_magic);
       int k = (int)l0 - jj * ne;
@@ -1152,14 +1268,22 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
           typename Phys2<float>::Beam b0, b1;
           load_beam<float>(et, ne, sigma, k, dut[tj], b0);
           load_beam<float>(et, ne, sigma, k + 1, dut[tj], b1);
-          F2 y2[3];
+          F2 y2[3], ep2[4];
 #pragma unroll
           for (int c = 0; c < 3; ++c) y2[c] = pk(ys[c][0], ys[c][1]);
+          if constexpr (kSplitLoad) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ep2[c] = pk(ep[c][0], ep[c][1]);
+          }
           const F2* rows = reinterpret_cast<const F2*>(tab) + (size_t)tj * (Phys::KT / 2);
           PairRK<Tab, kPass, kKind>::run(bs, pk(b0.eo, b1.eo), pk(b0.w, b1.w), rows,
-                                         n_jj * (Phys::KT / 2), y2, acc2, emax2, bad);
+                                         n_jj * (Phys::KT / 2), y2, ep2, acc2, emax2, bad);
 #pragma unroll
           for (int c = 0; c < 3; ++c) upk(y2[c], ys[c][0], ys[c][1]);
+          if constexpr (kSplitStore) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) upk(ep2[c], ep[c][0], ep[c][1]);
+          }
         }
       }
       if (!paired) {
@@ -1170,19 +1294,33 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
             const int tj = jj - (int)pc.jj_lo;
             typename Phys::Beam bm;
             load_beam<Real>(et, ne, sigma, k, dut[tj], bm);
-            Real y[NC];
+            Real y[NC], ev[NC + 1];
 #pragma unroll
             for (int c = 0; c < NC; ++c) y[c] = ys[c][v];
-            Body::beam(bs, bm, tv, tj, y, acc, emax, bad, mixed);
+            if constexpr (kSplitLoad) {
+#pragma unroll
+              for (int c = 0; c <= NC; ++c) ev[c] = ep[c][v];
+            }
+            Body::beam(bs, bm, tv, tj, y, ev, acc, emax, bad, mixed);
 #pragma unroll
             for (int c = 0; c < NC; ++c) ys[c][v] = y[c];
+            if constexpr (kSplitStore) {
+#pragma unroll
+              for (int c = 0; c <= NC; ++c) ep[c][v] = ev[c];
+            }
           }
           if (++k == ne) { k = 0; ++jj; }
         }
       }
-      if (kKind == kFinalPass) {
+      if constexpr (kKind == kFinalPass && !kSplitLoad) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) vstore(yout + (size_t)c * p.plane_stride + l0, ys[c]);
+      }
+      if constexpr (kSplitStore) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) vstore(yout + (size_t)c * p.plane_stride + l0, ys[c]);
+#pragma unroll
+        for (int c = 0; c <= NC; ++c) vstore(escr + (size_t)c * p.plane_stride + l0, ep[c]);
       }
     }
     if constexpr (kPair) {
@@ -1193,6 +1331,11 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
         acc[i] += a + b;
       }
       emax = fmax(emax, (Real)emax2);
+    }
+    // the pass forming Y_S also checked the step's input state (non-finite: fatal)
+    if constexpr (kSplitStore) {
+      const int any_bad = __syncthreads_or(bad);
+      if (any_bad && threadIdx.x == 0) atomicExch(&p.nonfinite[pc.inst], 1);
     }
     // reduce this piece into the instance accumulators
     if constexpr (sizeof(Real) == 4) {
@@ -1211,7 +1354,8 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
           float m = 0.0f;
           for (int w = 0; w < nw; ++w) m = fmaxf(m, redf[w]);
           if (any_bad) atomicExch(&p.nonfinite[pc.inst], 1);
-          atomicMax(&p.errmax[pc.inst], (unsigned long long)__double_as_longlong((double)m));
+          // the beams gave squared error ratios
+          atomicMax(&p.errmax[pc.inst], (unsigned long long)__double_as_longlong(sqrt((double)m)));
         }
       } else {
 #pragma unroll
@@ -1244,7 +1388,8 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       const double bmax = block_max(em, red);
       if (threadIdx.x == 0) {
         if (any_bad) atomicExch(&p.nonfinite[pc.inst], 1);
-        atomicMax(&p.errmax[pc.inst], (unsigned long long)__double_as_longlong(bmax));
+        // the beams gave squared error ratios
+        atomicMax(&p.errmax[pc.inst], (unsigned long long)__double_as_longlong(sqrt(bmax)));
       }
     } else {
       double v[NM];
