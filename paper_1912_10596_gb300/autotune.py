@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "_build", "autotune.json")
 
 # (block_size, blocks_per_sm): 768 or 512 resident threads per SM
-CANDIDATES_MIXED_2F = [(256, 3), (256, 2), (128, 6), (128, 4)]
+CANDIDATES_MIXED_2F = [(256, 3), (256, 2), (512, 1), (128, 6), (128, 4)]
 CANDIDATES_OTHER = [(256, 1), (128, 2)]
 
 

@@ -132,8 +132,8 @@ int check_config(const xflat_config& c, std::string& why) {
     why = "bad power-law matter parameters"; return XFLAT_ERR_INVAL;
   }
   if (c.matter_kind == XFLAT_MATTER_CONSTANT && !is_fin(c.lambda_const_kmi)) { why = "bad lambda_const"; return XFLAT_ERR_INVAL; }
-  if (c.block_size != 0 && c.block_size != 128 && c.block_size != 256) {
-    why = "block_size must be 0, 128 or 256"; return XFLAT_ERR_INVAL;
+  if (c.block_size != 0 && c.block_size != 128 && c.block_size != 256 && c.block_size != 512) {
+    why = "block_size must be 0, 128, 256 or 512"; return XFLAT_ERR_INVAL;
   }
   return XFLAT_OK;
 }
@@ -561,7 +561,7 @@ int setup_launch_shape(xflat_t h, const xflat_config& c) {
   // is built for one 256-thread block per SM.  Default: 256 threads x 3 blocks.
   h->block = c.block_size ? (int)c.block_size : 256;
   const int want_bps = c.blocks_per_sm ? (int)c.blocks_per_sm : (768 / h->block);
-  h->kernel = step_kernel_ptr(h->nf, h->precision, h->integrator, want_bps * h->block >= 768 ? 3 : 2);
+  h->kernel = step_kernel_ptr(h->nf, h->precision, h->integrator, h->block, want_bps * h->block >= 768 ? 3 : 2);
   if (!h->kernel) return fail(h, XFLAT_ERR_UNSUPPORTED, "no kernel for this flavour/precision/integrator");
   const size_t smax = smem_bytes(h->nf, h->real_size, max_jj_cap(h->nf, h->real_size));
   CUDA_TRY(h, cudaFuncSetAttribute(h->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));

@@ -3,7 +3,8 @@
 
 namespace xflat {
 struct KParams;
-// The __global__ step kernel for (n_flavor, precision, integrator) built for the requested number
-// of resident blocks per SM (mixed two-flavour kernels: 2 or 3; all others: 1), or nullptr.
-const void* step_kernel_ptr(int n_flavor, int precision, int integrator, int blocks_per_sm);
+// The __global__ step kernel for (n_flavor, precision, integrator) built for the requested block
+// size and resident blocks per SM (mixed two-flavour kernels: 256 x 2 or 3, or 512 x 1; all others:
+// up to 256 threads, one block), or nullptr.
+const void* step_kernel_ptr(int n_flavor, int precision, int integrator, int block, int blocks_per_sm);
 }  // namespace xflat

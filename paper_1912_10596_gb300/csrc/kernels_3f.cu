@@ -4,11 +4,11 @@
 
 namespace xflat {
 
-const void* step_kernel_ptr_2f(int precision, int integrator, int blocks_per_sm);
+const void* step_kernel_ptr_2f(int precision, int integrator, int block, int blocks_per_sm);
 
-const void* step_kernel_ptr(int n_flavor, int precision, int integrator, int blocks_per_sm) {
-  if (n_flavor == 2) return step_kernel_ptr_2f(precision, integrator, blocks_per_sm);
-  if (n_flavor != 3) return nullptr;
+const void* step_kernel_ptr(int n_flavor, int precision, int integrator, int block, int blocks_per_sm) {
+  if (n_flavor == 2) return step_kernel_ptr_2f(precision, integrator, block, blocks_per_sm);
+  if (n_flavor != 3 || block > 256) return nullptr;
   if (precision == 0) {
     if (integrator == kRK4) return (const void*)&step_kernel<Phys3<double>, TabRK4, double, false, 1>;
     if (integrator == kDP45) return (const void*)&step_kernel<Phys3<double>, TabDP45, double, false, 1>;

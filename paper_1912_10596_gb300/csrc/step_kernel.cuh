@@ -932,14 +932,16 @@ struct PairRK {
   static constexpr int kChain =
       kKind == kInitPass ? 0 : (kKind == kFinalPass ? Tab::S - (Tab::kAdaptive ? 1 : 0) : kPass + 1);
 
-  // K and -K of stage row R (packed values) for the pair's eta omega
+  // K and -K of stage row R (packed values) for the pair's eta omega; -K_x and -K_z by one packed
+  // multiply by (-1, -1) each, -K_y = -G0_y from the row
   __device__ static inline void Kpair(const F2* R, F2 eo, F2 (&K)[3], F2 (&nK)[3]) {
+    const F2 m1 = 0xbf800000bf800000ull;            // (-1.0f, -1.0f)
     K[0] = fma2(eo, R[P::vQBX], R[P::vG0X]);
     K[1] = R[P::vG0Y];
     K[2] = fma2(eo, R[P::vQBZ], R[P::vG0Z]);
-    nK[0] = fma2(eo, R[P::vNQBX], R[P::vNG0X]);
+    nK[0] = mul2(K[0], m1);
     nK[1] = R[P::vNG0Y];
-    nK[2] = fma2(eo, R[P::vNQBZ], R[P::vNG0Z]);
+    nK[2] = mul2(K[2], m1);
   }
   // k = K x Y as K1 Y2 - K2 Y1, ... with the products of -K added by FMA
   __device__ static inline void cross(const F2 (&K)[3], const F2 (&nK)[3], const F2 (&Y)[3], F2 (&k)[3]) {
@@ -969,6 +971,11 @@ struct PairRK {
   __device__ static inline void run(const BS& bs, F2 eo, F2 w, const F2* rows, int rstride, F2 (&y)[3],
                                     F2 (&ep)[4], F2 (&acc)[6], float& emax, int& bad) {
     F2 k[Tab::S + 1][3];
+    // adaptive final pass: y5 and the error accumulate as soon as each stage derivative exists
+    // (same order of operations as summing after the chain), so the derivatives die early
+    constexpr bool kFinalAdaptive = kKind == kFinalPass && Tab::kAdaptive;
+    F2 yn[3] = {y[0], y[1], y[2]};
+    F2 e[3] = {0ull, 0ull, 0ull};
 #pragma unroll
     for (int l = 1; l <= kChain; ++l) {
       F2 Y[3] = {y[0], y[1], y[2]};
@@ -982,6 +989,18 @@ struct PairRK {
       F2 K[3], nK[3];
       Kpair(rows + l * rstride, eo, K, nK);
       cross(K, nK, Y, k[l]);
+      if (kFinalAdaptive) {
+        if (Tab::b(l) != 0.0) {
+          const F2 hb = bs.hB2[l];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) yn[i] = fma2(hb, k[l][i], yn[i]);
+        }
+        if (Tab::e(l) != 0.0) {
+          const F2 he = bs.hE2[l];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) e[i] = fma2(he, k[l][i], e[i]);
+        }
+      }
     }
     if (kKind == kInitPass) {
       accum(acc, w, rows[rstride * 1 + P::vT1], y);
@@ -1004,14 +1023,6 @@ struct PairRK {
     if (Tab::kAdaptive) {
       // final pass: y5 from the rebuilt chain, k_S = f(y5), the embedded error and the squared
       // error ratio |e|_F^2 / scale^2 (its square root is taken once per block)
-      F2 yn[3] = {y[0], y[1], y[2]};
-#pragma unroll
-      for (int m = 1; m <= kChain; ++m)
-        if (Tab::b(m) != 0.0) {
-          const F2 hb = bs.hB2[m];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) yn[i] = fma2(hb, k[m][i], yn[i]);
-        }
       F2 n2y = mul2(y[0], y[0]);
       n2y = fma2(y[1], y[1], n2y);
       n2y = fma2(y[2], y[2], n2y);
@@ -1031,14 +1042,11 @@ struct PairRK {
       F2 K[3], nK[3];
       Kpair(rows + Tab::S * rstride, eo, K, nK);
       cross(K, nK, yn, k[Tab::S]);
-      F2 e[3] = {0ull, 0ull, 0ull};
+      if (Tab::e(Tab::S) != 0.0) {
+        const F2 he = bs.hE2[Tab::S];
 #pragma unroll
-      for (int m = 1; m <= Tab::S; ++m)
-        if (Tab::e(m) != 0.0) {
-          const F2 he = bs.hE2[m];
-#pragma unroll
-          for (int i = 0; i < 3; ++i) e[i] = fma2(he, k[m][i], e[i]);
-        }
+        for (int i = 0; i < 3; ++i) e[i] = fma2(he, k[Tab::S][i], e[i]);
+      }
       F2 e2 = mul2(e[0], e[0]);
       e2 = fma2(e[1], e[1], e2);
       e2 = fma2(e[2], e[2], e2);
@@ -1062,7 +1070,6 @@ struct PairRK {
       return;
     }
     // final pass of a fixed-step tableau
-    F2 yn[3] = {y[0], y[1], y[2]};
 #pragma unroll
     for (int m = 1; m <= kChain; ++m)
       if (Tab::b(m) != 0.0) {
@@ -1470,13 +1477,15 @@ __device__ __forceinline__ bool all_passes(const KParams& p, BlockShared<Real, P
   }
 }
 
-// kMinB: resident 256-thread blocks per SM the register budget is sized for.  FP64 work runs on
-// GB300's narrow FP64 pipe (about 1/68 of the FP32 rate), which one block per SM already keeps
-// busy, so FP64 kernels are built with kMinB = 1 (whole register file, no spills).  The FP32
-// two-flavour kernels are latency-bound; they are built for 2 and 3 blocks per SM and the launch
-// shape is chosen by measurement (the autotuner in paper_1912_10596_gb300/autotune.py).
-template <class Phys, class Tab, typename Real, bool kCF, int kMinB>
-__global__ void __launch_bounds__(256, kMinB) step_kernel(KParams p) {
+// kThreads x kMinB: the block size and resident blocks per SM the register budget is sized for.
+// FP64 work runs on GB300's narrow FP64 pipe (about 1/68 of the FP32 rate), which one 256-thread
+// block per SM already keeps busy, so FP64 kernels are built for that (whole register file, no
+// spills).  The FP32 two-flavour kernels are latency-bound; they are built for 768 resident threads
+// per SM (256 x 3) and for 512 (256 x 2, or one 512-thread block: the SM's two halves of the work
+// then finish together instead of the older block's warps finishing first), and the launch shape
+// is chosen by measurement (the autotuner in paper_1912_10596_gb300/autotune.py).
+template <class Phys, class Tab, typename Real, bool kCF, int kMinB, int kThreads = 256>
+__global__ void __launch_bounds__(kThreads, kMinB) step_kernel(KParams p) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ BlockShared<Real, Phys> bs;
   if (threadIdx.x == 0) {
