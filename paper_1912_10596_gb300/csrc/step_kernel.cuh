@@ -432,6 +432,27 @@ __device__ __forceinline__ void strengths(const InstConst& ic, double r, double&
   }
 }
 
+// Component c of a stage's moments: the kAccCopies fixed-point copies summed as integers (exact,
+// so every block that reads them gets the same bits), then converted to double.
+template <typename Real>
+__device__ __forceinline__ double acc_component(const unsigned long long* acc_slot, int c) {
+  if constexpr (sizeof(Real) == 4) {
+    long long sum = 0;
+#pragma unroll
+    for (int cp = 0; cp < kAccCopies; ++cp) sum += (long long)__ldcg(acc_slot + ((size_t)cp * kNMMax + c) * 2);
+    return (double)sum * 3.552713678800501e-15;                  // 2^-48
+  } else {
+    unsigned __int128 sum = 0;
+#pragma unroll
+    for (int cp = 0; cp < kAccCopies; ++cp) {
+      const unsigned long long* w = acc_slot + ((size_t)cp * kNMMax + c) * 2;
+      sum += ((unsigned __int128)__ldcg(w + 1) << 64) | (unsigned __int128)__ldcg(w);
+    }
+    return (double)(long long)(unsigned long long)(sum >> 64) +
+           (double)(unsigned long long)sum * 5.421010862427522e-20;    // 2^-64
+  }
+}
+
 template <class Phys, class Tab, typename Real>
 __device__ int serial_update(const KParams& p, int slot, bool final_pass, bool init) {
   constexpr int NM = Phys::NM;
@@ -448,25 +469,8 @@ __device__ int serial_update(const KParams& p, int slot, bool final_pass, bool i
     const unsigned long long eb = __ldcg(&p.errmax[i]);
     double m[NM];
     if (have_moments) {
-      // sum the accumulator copies as integers (exact), then convert
 #pragma unroll
-      for (int c = 0; c < NM; ++c) {
-        if constexpr (sizeof(Real) == 4) {
-          long long sum = 0;
-#pragma unroll
-          for (int cp = 0; cp < kAccCopies; ++cp) sum += (long long)__ldcg(acc + ((size_t)cp * kNMMax + c) * 2);
-          m[c] = (double)sum * 3.552713678800501e-15;        // 2^-48
-        } else {
-          unsigned __int128 sum = 0;
-#pragma unroll
-          for (int cp = 0; cp < kAccCopies; ++cp) {
-            const unsigned long long* w = acc + ((size_t)cp * kNMMax + c) * 2;
-            sum += ((unsigned __int128)__ldcg(w + 1) << 64) | (unsigned __int128)__ldcg(w);
-          }
-          m[c] = (double)(long long)(unsigned long long)(sum >> 64) +
-                 (double)(unsigned long long)sum * 5.421010862427522e-20;   // 2^-64
-        }
-      }
+      for (int c = 0; c < NM; ++c) m[c] = acc_component<Real>(acc, c);
     }
     double m7[NM], sc7[Phys::NSC];
     if (adaptive_final) {
@@ -954,13 +958,20 @@ struct PairRK {
 #pragma unroll
     for (int i = 0; i < 3; ++i) { acc[i] = fma2(wt, y[i], acc[i]); acc[3 + i] = fma2(w, y[i], acc[3 + i]); }
   }
+  // 1/sqrt(n2) of a pair: hardware reciprocal square root refined by one Newton step
+  // r <- r (3 - n2 r^2) / 2 (relative error ~1e-7, as a correctly rounded quotient would give)
+  __device__ static inline F2 rnorm(F2 n2) {
+    float a, b;
+    upk(n2, a, b);
+    const F2 r = pk(rsqrtf(a), rsqrtf(b));
+    const F2 t = mul2(mul2(n2, r), r);                         // n2 r^2
+    return mul2(mul2(r, 0xbf000000bf000000ull), fma2(t, 0x3f8000003f800000ull, 0xc0400000c0400000ull));
+  }
   __device__ static inline void normalise(F2 (&y)[3]) {
     F2 n2 = mul2(y[0], y[0]);
     n2 = fma2(y[1], y[1], n2);
     n2 = fma2(y[2], y[2], n2);
-    float a, b;
-    upk(n2, a, b);
-    const F2 inv = pk(1.0f / sqrtf(a), 1.0f / sqrtf(b));
+    const F2 inv = rnorm(n2);
 #pragma unroll
     for (int i = 0; i < 3; ++i) y[i] = mul2(y[i], inv);
   }
@@ -1035,7 +1046,7 @@ struct PairRK {
       if (!(a0 <= 3.0e38f) || !(a1 <= 3.0e38f)) bad = 1;    // non-finite input state: fatal
       const bool ok0 = c0 <= 3.0e38f, ok1 = c1 <= 3.0e38f;
       if (ok0 && ok1) {
-        const F2 inv = pk(1.0f / sqrtf(c0), 1.0f / sqrtf(c1));
+        const F2 inv = rnorm(n2n);
 #pragma unroll
         for (int i = 0; i < 3; ++i) yn[i] = mul2(yn[i], inv);
       }
@@ -1060,8 +1071,8 @@ struct PairRK {
       const float atol = bs.atol, rtol = bs.rtol;
       const float s0 = atol + rtol * sqrtf(0.5f * fmaxf(a0, m20));
       const float s1 = atol + rtol * sqrtf(0.5f * fmaxf(a1, m21));
-      float r0 = __fdiv_rn(0.5f * e20, s0 * s0);
-      float r1 = __fdiv_rn(0.5f * e21, s1 * s1);
+      float r0 = __fdividef(0.5f * e20, s0 * s0);
+      float r1 = __fdividef(0.5f * e21, s1 * s1);
       if (!(r0 <= 3.0e38f) || !ok0) r0 = INFINITY;
       if (!(r1 <= 3.0e38f) || !ok1) r1 = INFINITY;
       emax = fmaxf(emax, fmaxf(r0, r1));
@@ -1124,19 +1135,25 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
   Real* dut = tab + (size_t)kMaxStages * p.max_jj * Phys::KT;        // [max_jj]
   const bool mixed = sizeof(Real) == 4;
   const int slot = kKind == kInitPass ? 1 : (kKind == kStagePass ? kPass + 2 : 0);
-  // Clear the accumulator slot the previous barrier consumed (block 0, while the other blocks
-  // already work): before pass 0 the slots of the previous final pass (0) and of the initial
-  // reduction (1), before pass p the slot of stage p + 1.  Nothing accumulates into these slots
-  // until several barriers later, and block 0's stores are fenced at its next arrival.
+  // Clear accumulator slots nobody reads any more (block 0, while the other blocks already work).
+  // Stage s (2 <= s <= S) is reduced in pass s - 2 and read by every block in the set-up of pass
+  // s - 1, so it is cleared at the start of pass s (stage S: at the start of the next step's pass
+  // 0, with the final pass's slot 0 and the moment launch's slot 1, both read by serial updates
+  // that finish before their barrier opens).  Nothing accumulates into a cleared slot until at
+  // least one barrier later, and block 0's stores are fenced at its next arrival.
   if (kKind != kInitPass && blockIdx.x == 0) {
     constexpr int kWords = kAccCopies * kNMMax * 2;
-    for (int t = threadIdx.x; t < p.n_inst * 2 * kWords; t += blockDim.x) {
-      const int inst = t / (2 * kWords), rem = t % (2 * kWords);
-      const int zslot = kPass == 0 ? (rem < kWords ? 0 : 1) : (rem < kWords ? kPass + 1 : -1);
-      if (zslot >= 0) p.acc[(size_t)inst * kAccWordsPerInst + (size_t)zslot * kWords + rem % kWords] = 0ull;
+    constexpr int kSlots = kPass == 0 ? 3 : (kPass >= 2 ? 1 : 0);
+    for (int t = threadIdx.x; t < p.n_inst * kSlots * kWords; t += blockDim.x) {
+      const int inst = t / (kSlots * kWords), rem = t % (kSlots * kWords), q = rem / kWords;
+      const int zslot = kPass == 0 ? (q == 0 ? 0 : (q == 1 ? 1 : Tab::S)) : kPass;
+      p.acc[(size_t)inst * kAccWordsPerInst + (size_t)zslot * kWords + rem % kWords] = 0ull;
     }
   }
   const unsigned need = stages_needed<Tab, kPass, kKind>();
+  // the stage whose moments the previous pass reduced (0: none of this step, its constants come
+  // from the serial update of the previous step or of the moment launch)
+  constexpr int kNewest = (kKind != kInitPass && kPass >= 1) ? kPass + 1 : 0;
   const int b0 = p.blk_piece[blockIdx.x], b1 = p.blk_piece[blockIdx.x + 1];
   for (int pi = b0; pi < b1; ++pi) {
     const Piece pc = p.pieces[pi];
@@ -1151,7 +1168,26 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     const double h = Tab::kAdaptive ? ldcg(&d->h) : ldcg(&d->h_fixed);
     for (int t = threadIdx.x; t < kMaxStages * Phys::NSC; t += blockDim.x) {
       const int s = t / Phys::NSC, c = t % Phys::NSC;
-      const double v = ((need >> s) & 1u) ? ldcg(&d->sc[s][c]) : 0.0;
+      double v = 0.0;
+      if (s == kNewest) {
+        // the stage reduced by the previous pass: every block derives its constants mu m (and
+        // lambda) from the accumulators itself (integer sums: the same bits everywhere), so that
+        // barrier needs no serial section; the block holding the instance's first beams records
+        // the moments and constants for later passes and the host
+        const unsigned long long* accs = p.acc + (size_t)pc.inst * kAccWordsPerInst +
+                                         (size_t)s * kAccCopies * kNMMax * 2;
+        InstDyn* dw = p.dyn + pc.inst;
+        if (c < Phys::NM) {
+          const double m = acc_component<Real>(accs, c);
+          v = ldcg(&d->mus[s]) * m;
+          if (pc.start == 0) dw->mom[s][c] = m;
+        } else if (c == Phys::NM) {
+          v = ldcg(&d->lams[s]);
+        }
+        if (pc.start == 0 && c <= Phys::NM) dw->sc[s][c] = v;
+      } else if ((need >> s) & 1u) {
+        v = ldcg(&d->sc[s][c]);
+      }
       bs.scd[s][c] = v;
       bs.scr[s][c] = (Real)v;
     }
@@ -1447,17 +1483,25 @@ __device__ __forceinline__ bool pass_and_sync(const KParams& p, BlockShared<Real
       t[3] = (res & 0xf) == kBarLast ? 1ull : 0ull;
     }
   }
-  if ((res & 0xf) == kBarLast) {
-    const int mine = serial_update<Phys, Tab, Real>(p, kFinal ? 0 : kPass + 2, kFinal, false);
+  if ((res & 0xf) == kBarLast && !kFinal) {
+    // stage pass: every block derives the new stage's constants from the accumulators in its next
+    // set-up (run_pass), so the barrier opens at once (a non-finite partial is reported by the
+    // final pass's serial update)
+    if (threadIdx.x == 0) bs.flag = 0;
+    barrier_release(p.bar, 0, &bs.gen_seen);
+    if (p.trace && threadIdx.x == 0 && bs.pass_idx - 1 < p.trace_passes)
+      p.trace[((size_t)(bs.pass_idx - 1) * gridDim.x + blockIdx.x) * 4 + 3] = globaltimer_ns() | (1ull << 63);
+  } else if ((res & 0xf) == kBarLast) {
+    const int mine = serial_update<Phys, Tab, Real>(p, 0, true, false);
     const int all = __syncthreads_and(mine);
-    if (kFinal) serial_geometry<Tab>(p);
+    serial_geometry<Tab>(p);
     if (threadIdx.x == 0) {
-      if (kFinal) *p.all_done = all;
-      bs.flag = (kFinal && all) ? 0x10 : 0;
+      *p.all_done = all;
+      bs.flag = all ? 0x10 : 0;
     }
     unsigned long long ts = 0;
     if (p.trace && threadIdx.x == 0) ts = globaltimer_ns();
-    barrier_release(p.bar, kFinal ? all : 0, &bs.gen_seen);
+    barrier_release(p.bar, all, &bs.gen_seen);
     if (p.trace && threadIdx.x == 0 && bs.pass_idx - 1 < p.trace_passes) {
       // last block: stamp 3 = serial work done (bits 0..62), stamp 2 stays its arrival
       p.trace[((size_t)(bs.pass_idx - 1) * gridDim.x + blockIdx.x) * 4 + 3] = ts | (1ull << 63);
