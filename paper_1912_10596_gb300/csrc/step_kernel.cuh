@@ -420,8 +420,8 @@ __device__ __forceinline__ double controller_factor(double err) {
 }
 
 // mu(r) and lambda(r) at one radius (double).
-__device__ __forceinline__ void strengths(const InstConst& ic, double r, double& mu, double& lam) {
-  const double inv = 1.0 / r;
+// mu(r) and lambda(r) from 1/r
+__device__ __forceinline__ void strengths_inv(const InstConst& ic, double inv, double& mu, double& lam) {
   mu = ic.mu_coef * inv * inv;
   lam = 0.0;
   if (ic.matter == kMatterPower) {
@@ -431,6 +431,13 @@ __device__ __forceinline__ void strengths(const InstConst& ic, double r, double&
     lam = ic.lam_const;
   }
 }
+__device__ __forceinline__ void strengths(const InstConst& ic, double r, double& mu, double& lam) {
+  strengths_inv(ic, 1.0 / r, mu, lam);
+}
+
+// Loads that must not hit a stale L1 line: instance dynamics change across barriers.
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
 
 // Component c of a stage's moments: the kAccCopies fixed-point copies summed as integers (exact,
 // so every block that reads them gets the same bits), then converted to double.
@@ -451,6 +458,19 @@ __device__ __forceinline__ double acc_component(const unsigned long long* acc_sl
     return (double)(long long)(unsigned long long)(sum >> 64) +
            (double)(unsigned long long)sum * 5.421010862427522e-20;    // 2^-64
   }
+}
+
+// Hand-off of each instance's new r and h (and whether its next step needs stage geometry) from
+// serial_update to serial_geometry inside the last block, through shared memory (instances past
+// kGeoShared are read back from global memory).
+constexpr int kGeoShared = 64;
+struct GeoHandoff {
+  double r[kGeoShared], h[kGeoShared];
+  int pending[kGeoShared];
+};
+__device__ __forceinline__ GeoHandoff& geo_handoff() {
+  __shared__ GeoHandoff g;
+  return g;
 }
 
 template <class Phys, class Tab, typename Real>
@@ -558,6 +578,12 @@ __device__ int serial_update(const KParams& p, int slot, bool final_pass, bool i
       if (last) hh = r_end - r;
     }
     d.geo_pending = (!fin && !step_err) ? 1 : 0;
+    if (i < kGeoShared) {
+      GeoHandoff& g = geo_handoff();
+      g.r[i] = r;
+      g.h[i] = Tab::kAdaptive ? hh : hf;
+      g.pending[i] = d.geo_pending;
+    }
     d.r = r;
     d.h = hh;
     d.last = last;
@@ -569,38 +595,36 @@ __device__ int serial_update(const KParams& p, int slot, bool final_pass, bool i
     if (fin) d.done = 1;
     if (!fin && !step_err) all_finished = 0;
   }
-  if (threadIdx.x < p.n_inst) __threadfence();    // results visible before the barrier release
   return all_finished;
 }
 
 // The next step's stage radii, R^2/r^2, mu and lambda, one (instance, stage) per thread of the last
 // block: FP64 divisions have a long latency on this part, so they run side by side, not in a chain.
-// Reads the r, h and geo_pending that serial_update wrote in this block before a __syncthreads.
+// Takes r, h and the pending flag from serial_update (after a __syncthreads), then fences every
+// thread's writes (those of serial_update included) before the barrier is released.
 template <class Tab>
 __device__ void serial_geometry(const KParams& p) {
-  bool wrote = false;
+  const GeoHandoff& g = geo_handoff();
   for (int t = threadIdx.x; t < p.n_inst * Tab::S; t += blockDim.x) {
     const int i = t / Tab::S, s = t % Tab::S + 1;
     InstDyn& d = p.dyn[i];
-    if (!d.geo_pending) continue;
+    const bool shared = i < kGeoShared;
+    if (!(shared ? g.pending[i] : ldcg(&d.geo_pending))) continue;
     const InstConst& ic = p.ic[i];
-    const double r = d.r, h = Tab::kAdaptive ? d.h : d.h_fixed;
+    const double r = shared ? g.r[i] : ldcg(&d.r);
+    const double h = shared ? g.h[i] : (Tab::kAdaptive ? ldcg(&d.h) : ldcg(&d.h_fixed));
     const double rs = (s == 1) ? r : __dadd_rn(r, __dmul_rn(stage_c<Tab>(s), h));
+    const double inv = 1.0 / rs;
     double mus, lams;
-    strengths(ic, rs, mus, lams);
+    strengths_inv(ic, inv, mus, lams);
     d.rs[s] = rs;
-    d.xs[s] = ic.R2 / (rs * rs);
+    d.xs[s] = ic.R2 * inv * inv;
     d.mus[s] = mus;
     d.lams[s] = lams;
-    wrote = true;
   }
-  if (wrote) __threadfence();
+  __threadfence();
 }
 
-// ------------------------------------------------------------------------------------------
-// Loads that must not hit a stale L1 line: instance dynamics change across barriers.
-__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
-__device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
 
 // Per-thread state vectors: two consecutive beams per load (float2 / double2), so the loaded and
 // the prefetched vectors fit the register budget; a warp still reads 256 or 512 contiguous bytes
