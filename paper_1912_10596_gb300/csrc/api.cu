@@ -407,7 +407,8 @@ uint32_t max_jj_cap(int nf, size_t real_size) { return (nf == 2 && real_size == 
 size_t smem_bytes(int nf, size_t real_size, int max_jj) {
   size_t s = 32 * kNMMax * sizeof(double);
   s += (size_t)kMaxStages * max_jj * table_row_values(nf, real_size) * real_size;
-  s += (size_t)max_jj * real_size;
+  s += (size_t)max_jj * real_size;                 // angle weights
+  s = (s + 7) / 8 * 8 + (size_t)max_jj * sizeof(double);   // angle positions
   return (s + 15) / 16 * 16;
 }
 

@@ -1157,6 +1157,8 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
   double* red = reinterpret_cast<double*>(dyn_smem);                 // 32 * NM doubles
   Real* tab = reinterpret_cast<Real*>(red + 32 * kNMMax);            // [kMaxStages][max_jj][KT]
   Real* dut = tab + (size_t)kMaxStages * p.max_jj * Phys::KT;        // [max_jj]
+  double* ut = reinterpret_cast<double*>(                            // [max_jj], 8-byte aligned
+      (reinterpret_cast<uintptr_t>(dut + p.max_jj) + 7) & ~uintptr_t(7));
   const bool mixed = sizeof(Real) == 4;
   const int slot = kKind == kInitPass ? 1 : (kKind == kStagePass ? kPass + 2 : 0);
   // Clear accumulator slots nobody reads any more (block 0, while the other blocks already work).
@@ -1179,11 +1181,36 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
   // from the serial update of the previous step or of the moment launch)
   constexpr int kNewest = (kKind != kInitPass && kPass >= 1) ? kPass + 1 : 0;
   const int b0 = p.blk_piece[blockIdx.x], b1 = p.blk_piece[blockIdx.x + 1];
+  // A block with a single piece keeps its set-up in shared memory for the whole step: after pass
+  // 0 only the newest stage's constants and the table rows of the newest and the formed stage
+  // change (flags, step size, coefficients, radii, angle tables and older rows stay valid).
+  const bool incremental = (b1 - b0 == 1) && kNewest >= 1;
   for (int pi = b0; pi < b1; ++pi) {
     const Piece pc = p.pieces[pi];
     const InstConst& ic = p.ic[pc.inst];
     const InstDyn* d = p.dyn + pc.inst;
     __syncthreads();
+    if (incremental) {
+      if (threadIdx.x < Phys::NSC) {
+        const int c = threadIdx.x;
+        double v = 0.0;
+        const unsigned long long* accs = p.acc + (size_t)pc.inst * kAccWordsPerInst +
+                                         (size_t)kNewest * kAccCopies * kNMMax * 2;
+        InstDyn* dw = p.dyn + pc.inst;
+        if (c < Phys::NM) {
+          const double m = acc_component<Real>(accs, c);
+          v = ldcg(&d->mus[kNewest]) * m;
+          if (pc.start == 0) dw->mom[kNewest][c] = m;
+        } else if (c == Phys::NM) {
+          v = ldcg(&d->lams[kNewest]);
+        }
+        if (pc.start == 0 && c <= Phys::NM) dw->sc[kNewest][c] = v;
+        bs.scd[kNewest][c] = v;
+        bs.scr[kNewest][c] = (Real)v;
+      }
+      __syncthreads();
+    }
+    if (!incremental) {
     // one parallel load phase: flags, step size, stage constants, radii, angle weights
     if (threadIdx.x == 0) {
       bs.active = (ldcg(&d->done) == 0 && ldcg(&d->status) == 0) ? 1 : 0;
@@ -1243,13 +1270,15 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       bs.rtol = (Real)ic.rtol;
       bs.atol = (Real)ic.atol;
     }
-    const int n_jj = pc.n_jj;
-    for (int t = threadIdx.x; t < n_jj; t += blockDim.x) {
+    for (int t = threadIdx.x; t < (int)pc.n_jj; t += blockDim.x) {
       const int jj = pc.jj_lo + t;
       const int j = jj >= (int)ic.n_angle ? jj - (int)ic.n_angle : jj;
       dut[t] = (Real)p.du_tab[ic.a_off + j];
+      ut[t] = p.u_tab[ic.a_off + j];
     }
     __syncthreads();
+    }
+    const int n_jj = pc.n_jj;
     if (!bs.active) continue;
     typename Phys::Consts C;
     if constexpr (Phys::NC == 3) {
@@ -1258,18 +1287,18 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
 #pragma unroll
       for (int i = 0; i < 6; ++i) { C.M21[i] = ic.M21[i]; C.M31[i] = ic.M31[i]; }
     }
+    // table rows: every needed stage, or (incremental) only the newest and the formed stage
+    const unsigned fill = incremental ? (need & (3u << kNewest)) : need;
     for (int t = threadIdx.x; t < kMaxStages * n_jj; t += blockDim.x) {
       const int s = t / n_jj, tj = t % n_jj;
-      if (!((need >> s) & 1u)) continue;
-      const int jj = pc.jj_lo + tj;
-      const int j = jj >= (int)ic.n_angle ? jj - (int)ic.n_angle : jj;
+      if (!((fill >> s) & 1u)) continue;
       Real* row = tab + ((size_t)s * n_jj + tj) * Phys::KT;
       if constexpr (sizeof(Real) == 4) {
         float q, t1, t2;
-        geometry_f(p.u_tab[ic.a_off + j], bs.xs[s], q, t1, t2);
+        geometry_f(ut[tj], bs.xs[s], q, t1, t2);
         Phys::fill_f(row, q, t1, t2, bs.scr[s], C);
       } else {
-        Phys::fill(row, geometry(p.u_tab[ic.a_off + j], bs.xs[s]), bs.scd[s], C);
+        Phys::fill(row, geometry(ut[tj], bs.xs[s]), bs.scd[s], C);
       }
     }
     __syncthreads();
