@@ -1211,10 +1211,12 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       __syncthreads();
     }
     if (!incremental) {
-    // one parallel load phase: flags, step size, stage constants, radii, angle weights
+    // one parallel load phase: flags, step size, stage constants, radii, angle weights (every
+    // load issued before any of them is used, so the phase costs one L2 round trip)
     if (threadIdx.x == 0) {
-      bs.active = (ldcg(&d->done) == 0 && ldcg(&d->status) == 0) ? 1 : 0;
-      bs.parity = ldcg(&d->parity);
+      const int dn = ldcg(&d->done), st = ldcg(&d->status), par = ldcg(&d->parity);
+      bs.active = (dn == 0 && st == 0) ? 1 : 0;
+      bs.parity = par;
     }
     const double h = Tab::kAdaptive ? ldcg(&d->h) : ldcg(&d->h_fixed);
     for (int t = threadIdx.x; t < kMaxStages * Phys::NSC; t += blockDim.x) {
