@@ -30,22 +30,23 @@ from bulb_inputs import workload_2f_large  # noqa: E402
 BYTES_PER_BEAM_STAGE = {("mixed", "dp45"): 14.0, ("fp64", "dp45"): 28.0,
                         ("mixed", "rk4"): 15.0, ("fp64", "rk4"): 30.0}
 L2_BYTES = 129 * 1024 * 1024
-# DRAM traffic of one step launch of the timed kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture, profiles/step_kernel_mixed_dp45_4M.md).  It holds only
-# for the kernel sources it was taken on, identified by their SHA-256; after any change to them the
-# benchmark reports null until a new capture is recorded here.
-STEP_TRAFFIC = {"bytes": 55.03e6,
-                "sources_sha256": "7f5a6a22d6af2305af8c3525b30206c3b5a4f5c5d211c23e9eb5e0c27be37fd1"}
+# DRAM traffic of one timed launch of the step kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of an 8-step launch after the L2 flush,
+# profiles/step_kernel_mixed_dp45_4M.md).  It holds only for that launch size and for the kernel
+# sources it was taken on, identified by their SHA-256; otherwise the benchmark reports null.
+STEP_TRAFFIC = {"bytes_per_launch": 58393600 + 188043776, "steps_per_launch": 8,
+                "sources_sha256": "7cfb8b3b5c14f9bf3d6872b3544f84b811e49bbf2697db3de426d8db6f0e5d11"}
 KERNEL_SOURCES = ["step_kernel.cuh", "xflat_internal.cuh", "kernels_2f.cu"]
 
 
-def step_traffic():
+def step_traffic(steps_per_launch):
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1912_10596_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return STEP_TRAFFIC["bytes"] if h.hexdigest() == STEP_TRAFFIC["sources_sha256"] else None
+    ok = h.hexdigest() == STEP_TRAFFIC["sources_sha256"] and steps_per_launch == STEP_TRAFFIC["steps_per_launch"]
+    return STEP_TRAFFIC["bytes_per_launch"] if ok else None
 METRIC = "beam-updates/s (beams x RK stages)"
 
 
@@ -312,8 +313,10 @@ def main():
                        "grid_blocks": st.grid_blocks, "block_size": st.block_size,
                        "autotuned_shape": list(shape) if shape else None},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": step_traffic(),
-                         "note": f"{BYTES_PER_BEAM_STAGE[('mixed', 'dp45')]} algorithmic B per beam-stage; peak {peak_kind}"},
+                         "frac": achieved / hbm, "traffic": step_traffic(spl),
+                         "note": f"{BYTES_PER_BEAM_STAGE[('mixed', 'dp45')]} algorithmic B per beam-stage "
+                                 f"({BYTES_PER_BEAM_STAGE[('mixed', 'dp45')] * bsu * spl / 1e9:.2f} GB per {spl}-step launch); "
+                                 f"traffic = DRAM bytes per {spl}-step launch; peak {peak_kind}"},
             "clocks": clocks,
             "gpu_launches": len(chunks),
             "fp64_path": fp64,
