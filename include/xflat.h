@@ -220,6 +220,15 @@ int xflat_set_rho_inst(xflat_t h, uint32_t inst, const void* src, int src_is_dev
 int xflat_pee(xflat_t h, double* pee_per_beam, double* pee_mean);
 int xflat_pee_inst(xflat_t h, uint32_t inst, double* pee_per_beam, double* pee_mean);
 
+/* Energy spectra of the number flux at the current radius of instance inst (the nu_e flux of the
+ * Sec. 3.4 validation figure), summed over angle bins with their weights du_j:
+ *   flux[s][a][k] = sum_j du_j [ N[s][e][k] P_ea(s, j, k) + N[s][x][k] (1 - P_ea(s, j, k)) ],
+ * s = 0 nu, 1 nubar; a the flavour (e, x or e, mu, tau); P_ea the a-a entry of the density matrix
+ * of the beam that started as electron flavour (the other initial flavours, all with spectrum
+ * N[s][x], carry 1 - P_ea into flavour a by unitarity).  flux: caller-owned host array of
+ * 2 n_flavor n_energy doubles, in the units of N.  At r = R: flux[s][e] = N[s][e] sum_j du_j. */
+int xflat_flux_spectra(xflat_t h, uint32_t inst, double* flux);
+
 int xflat_get_stats(xflat_t h, xflat_stats* out);
 int xflat_get_stats_inst(xflat_t h, uint32_t inst, xflat_stats* out);
 

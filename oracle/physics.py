@@ -253,6 +253,19 @@ class Bulb:
         W = self.grid.du[:, None] * self.grid.N[0, 0][None, :]
         return float((W * Y[0, ..., 0, 0].real).sum() / W.sum())
 
+    def flux_spectra(self, Y: np.ndarray) -> np.ndarray:
+        """Number-flux energy spectra [2, n, N_E] of every flavour (the nu_e flux of the Sec. 3.4
+        validation figure): Phi_a(E_k) = sum_j du_j [N_e,k P_aa + N_x,k (1 - P_aa)], P the density
+        matrix of the beam that started as electron flavour (nu: P, nubar: Pbar), the beams that
+        started as the other flavours carrying 1 - P_aa into flavour a by unitarity."""
+        N, du = self.grid.N, self.grid.du
+        out = np.zeros((2, self.n, len(self.grid.E)))
+        for s in range(2):
+            diag = np.einsum("jkaa->ajk", Y[s]).real                       # [n, N_u, N_E]
+            out[s] = np.einsum("j,ajk->ak", du, N[s, 0][None, None, :] * diag
+                               + N[s, 1][None, None, :] * (1.0 - diag))
+        return out
+
     def moment_matrices(self, r: float, Y: np.ndarray):
         """Traceless parts of J0 = sum_b du F_b / cos th_b and J1 = sum_b du F_b (matrix form).
 

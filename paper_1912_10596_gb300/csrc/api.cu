@@ -267,6 +267,31 @@ __global__ void k_pee_mean(const double* pee, const double* N_e, const double* d
   if (threadIdx.x == 0) out[0] = sd[0] > 0 ? sn[0] / sd[0] : 0.0;
 }
 
+// Number-flux energy spectra: one thread per (species, flavour a, energy k), angle bins summed in
+// order: Phi = sum_j du_j [N_e P_ea + N_x (1 - P_ea)], P_ea the a-a entry of the electron-flavour
+// state (unitarity: the x states carry 1 - P_ea into flavour a).
+template <typename Real>
+__global__ void k_flux_spectra(const Real* src, uint64_t stride, uint32_t ne, uint32_t na, int nf,
+                               const double* N, const double* du, double* flux) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2u * nf * ne) return;
+  const uint32_t sig = t / (nf * ne), a = (t / ne) % nf, k = t % ne;
+  const double Ne = N[(sig * nf + 0) * ne + k], Nx = N[(sig * nf + 1) * ne + k];
+  double f = 0.0;
+  for (uint32_t j = 0; j < na; ++j) {
+    const uint64_t b = ((uint64_t)sig * na + j) * ne + k;
+    double P;
+    if (nf == 2) {
+      const double sz = (double)src[2 * stride + b];
+      P = a == 0 ? 0.5 * (1.0 + sz) : 0.5 * (1.0 - sz);
+    } else {
+      P = (double)src[(uint64_t)a * stride + b];
+    }
+    f += du[j] * (Ne * P + Nx * (1.0 - P));
+  }
+  flux[t] = f;
+}
+
 // ---- host helpers ------------------------------------------------------------------------------
 void build_tables(xflat_t h, HostInst& I, std::vector<double>& et, InstConst& ic) {
   const xflat_config& c = I.cfg;
@@ -1047,6 +1072,30 @@ int xflat_pee_inst(xflat_t h, uint32_t inst, double* pee_per_beam, double* pee_m
 
 int xflat_pee(xflat_t h, double* pee_per_beam, double* pee_mean) {
   return xflat_pee_inst(h, 0, pee_per_beam, pee_mean);
+}
+
+int xflat_flux_spectra(xflat_t h, uint32_t inst, double* flux) {
+  if (!h || !flux) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
+  if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
+  if (!h->inst[inst].spectra) return fail(h, XFLAT_ERR_STATE, "set_spectra first");
+  int rc;
+  if ((rc = download_dyn(h))) return rc;
+  const HostInst& I = h->inst[inst];
+  const uint32_t ne = I.cfg.n_energy, na = I.cfg.n_angle;
+  const int nf = h->nf;
+  const size_t nval = 2ull * nf * ne;
+  if ((rc = ensure_stage(h, 2 * nval * sizeof(double)))) return rc;
+  double* dN = h->d_stage;
+  double* dflux = dN + nval;
+  CUDA_TRY(h, cudaMemcpyAsync(dN, I.N.data(), nval * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  const void* src = cur_plane(h, inst);
+  const unsigned nb = (unsigned)((nval + 127) / 128);
+  if (h->real_size == 8) k_flux_spectra<double><<<nb, 128, 0, h->stream>>>((const double*)src, h->stride, ne, na, nf, dN, h->d_du + I.a_off, dflux);
+  else k_flux_spectra<float><<<nb, 128, 0, h->stream>>>((const float*)src, h->stride, ne, na, nf, dN, h->d_du + I.a_off, dflux);
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaMemcpyAsync(flux, dflux, nval * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return XFLAT_OK;
 }
 
 int xflat_get_stats_inst(xflat_t h, uint32_t inst, xflat_stats* out) {

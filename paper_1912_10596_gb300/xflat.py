@@ -76,6 +76,7 @@ _SIGS = {
     "xflat_set_rho_inst": (_H, C.c_uint32, _P, C.c_int, C.c_int, C.c_double),
     "xflat_pee": (_H, _P, _P),
     "xflat_pee_inst": (_H, C.c_uint32, _P, _P),
+    "xflat_flux_spectra": (_H, C.c_uint32, _P),
     "xflat_get_stats": (_H, C.POINTER(xflat_stats)),
     "xflat_get_stats_inst": (_H, C.c_uint32, C.POINTER(xflat_stats)),
     "xflat_adjoint": (_H, C.c_double, C.c_double, C.c_uint32, C.c_uint32, _P, _P, _P),
@@ -245,6 +246,13 @@ class Solver:
         mean = np.zeros(1)
         _check(_lib.xflat_pee_inst(self.h, inst, _ptr(out), _ptr(mean)), self.h)
         return out, float(mean[0])
+
+    def flux_spectra(self, inst=0):
+        """Number-flux energy spectra [2, n_flavor, n_energy] at the current radius."""
+        c = self.cfgs[inst]
+        out = np.zeros(2 * c.n_flavor * c.n_energy)
+        _check(_lib.xflat_flux_spectra(self.h, inst, _ptr(out)), self.h)
+        return out.reshape(2, c.n_flavor, c.n_energy)
 
     def stats(self, inst=0) -> xflat_stats:
         s = xflat_stats()

@@ -394,3 +394,88 @@ def test_order_sensitivity_floor():
     floor = float((np.sqrt((np.abs(A - B) ** 2).sum(axis=(-2, -1)))
                    / np.sqrt((np.abs(A) ** 2).sum(axis=(-2, -1)))).max())
     assert 0.0 < floor < 1e-11, floor
+
+
+@pytest.mark.parametrize("nf", [2, 3])
+def test_flux_spectra_pins(nf):
+    """Flux spectra: the initial condition gives the emitted spectra; every state conserves the
+    total number per energy bin (unitarity); equal e and x spectra hide any flavour change; the
+    vacuum closed form fixes the nu_e flux of an evolved state."""
+    kw = dict(n_flavor=3, dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.785)) if nf == 3 else {}
+    wl = Workload(name="fx", n_energy=6, n_angle=5, **kw)
+    b = Bulb(wl)
+    g = b.grid
+    F0 = b.flux_spectra(b.initial_state())
+    sdu = g.du.sum()
+    for s in range(2):
+        assert np.allclose(F0[s, 0], g.N[s, 0] * sdu, rtol=1e-15)
+        for a in range(1, nf):
+            assert np.allclose(F0[s, a], g.N[s, 1] * sdu, rtol=1e-15)
+    psi = np.random.default_rng(3).standard_normal((2, 5, 6, nf)) + 1j * np.random.default_rng(4).standard_normal((2, 5, 6, nf))
+    psi /= np.linalg.norm(psi, axis=-1, keepdims=True)
+    Y = psi[..., :, None] * np.conj(psi[..., None, :])
+    F = b.flux_spectra(Y)
+    for s in range(2):
+        assert np.allclose(F[s].sum(axis=0), (g.N[s, 0] + (nf - 1) * g.N[s, 1]) * sdu, rtol=1e-13)
+    Neq = g.N.copy()
+    Neq[:, 0] = Neq[:, 1]
+    beq = Bulb(wl, grid=Grid(E=g.E, u=g.u, du=g.du, N=Neq))
+    assert np.allclose(beq.flux_spectra(Y)[:, 0], Neq[:, 0] * sdu, rtol=1e-13)
+    if nf == 2:
+        # vacuum: P_ee of the closed form at path length L_j, then Phi_e by hand
+        wv = Workload(name="fxv", n_energy=6, n_angle=5, L={k: 0.0 for k in ("nue", "nuebar", "nux", "nuxbar")},
+                      dm2=(2.4e-3, 0.0), theta=(0.3, 0, 0))
+        bv = Bulb(wv, grid=Grid(E=g.E, u=g.u, du=g.du, N=np.zeros_like(g.N)))
+        Yv, _ = evolve_fixed(bv, bv.initial_state(), 11.0, 31.0, 4000, method="lie_rk4")
+        bv = Bulb(wv, grid=g)             # the flux weights of the emitted spectra
+        c = np.sqrt(1 - g.u * 121.0 / 31.0**2)
+        Lp = 31.0 * c - 11.0 * np.sqrt(1 - g.u)
+        pee = 1 - np.sin(0.6) ** 2 * np.sin(2.4e-3 * Lp[:, None] / (4 * g.E[None, :] * 1e6 * 197.3269804e-12)) ** 2
+        want = (g.du[:, None] * (g.N[0, 0][None] * pee + g.N[0, 1][None] * (1 - pee))).sum(axis=0)
+        assert np.allclose(bv.flux_spectra(Yv)[0, 0], want, rtol=1e-10)
+
+
+# --- exponential midpoint rule (the paper's kind of integrator) ------------------------------------
+def test_em2_order_and_embedded_error():
+    """Richardson: the exponential midpoint rule is second order, its exponential-Euler partner
+    first order, so their difference (the error estimate) shrinks like h^2 per step."""
+    from oracle.integrate import evolve_em2, em2_step
+    b, Y0 = _nonlinear_case()
+    Yref, _ = evolve_fixed(b, Y0, 80.0, 82.0, 8000, "rk4")
+    errs = []
+    for n in (200, 400, 800):
+        Y, _, _ = evolve_em2(b, Y0, 80.0, 82.0, 1, 1, 1, fixed_steps=n)
+        errs.append(np.abs(Y - Yref).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(q - 2) < 0.25 for q in rates), (errs, rates)
+    loc = []
+    for h in (0.02, 0.01, 0.005):
+        Yn, Ye = em2_step(b.generators, 80.0, Y0, h)
+        loc.append(np.abs(Yn - Ye).max())
+    lr = [math.log2(loc[i] / loc[i + 1]) for i in range(2)]
+    assert all(abs(q - 2) < 0.25 for q in lr), (loc, lr)
+
+
+def test_em2_exact_for_constant_generator():
+    """A generator that does not change (vacuum + constant matter, no nu-nu coupling (mu0 = 0), all
+    beams radial in the homogeneous test geometry) is integrated exactly, and the error estimate
+    vanishes."""
+    from oracle.integrate import em2_step
+    wl = Workload(name="cst", n_energy=4, n_angle=3, matter="constant", lambda_const=3.0,
+                  dm2=(2.4e-3, 0.0), theta=(0.3, 0, 0))
+    b = Bulb(wl, geometry="homogeneous", mu0=0.0)
+    Y0 = b.initial_state()
+    Yn, Ye = em2_step(b.generators, 50.0, Y0, 0.37)
+    G = b.generators(50.0, Y0)
+    U = np.stack([expm(-1j * 0.37 * g) for g in G.reshape(-1, 2, 2)]).reshape(G.shape)
+    exact = U @ Y0 @ np.conj(np.swapaxes(U, -1, -2))
+    assert np.abs(Yn - exact).max() < 1e-13 and np.abs(Yn - Ye).max() < 1e-13
+
+
+def test_em2_adaptive_meets_tolerance():
+    from oracle.integrate import evolve_em2
+    b, Y0 = _nonlinear_case()
+    Yref, _ = evolve_fixed(b, Y0, 80.0, 82.0, 8000, "rk4")
+    Y, r, st = evolve_em2(b, Y0, 80.0, 82.0, 1e-7, 1e-7, 1e-3)
+    assert r == 82.0 and st.rejected >= 0 and st.accepted > 20
+    assert np.abs(Y - Yref).max() < 1e-4
