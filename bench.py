@@ -206,6 +206,51 @@ def cpu_baseline(seconds=12.0, impl_steps=None):
     return beams * 6 * n / dt, n, dt, beams
 
 
+def compare_integrators():
+    """Accuracy against cost of the integrators on the 4096-beam case (64 E x 32 u, FP64) over a
+    window of strong collective evolution (100 -> 110 km): the exponential midpoint rule (the
+    paper's kind of scheme: exact Eq. U propagators with a mid-point rule and adaptive steps),
+    Dormand-Prince 5(4) and the fixed-step commutator-free Lie RK4, against a DP45 reference at
+    rtol = atol = 1e-12.  One JSON line per run: max |P_ee - P_ee,ref| over all beams, stage
+    evaluations, accepted / rejected steps, device time (CUDA events around xflat_evolve)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_10596_gb300 import xflat as xf
+    from bulb_inputs import workload_2f_small_fp64
+    wl = workload_2f_small_fp64()
+    r0, r1 = 100.0, 110.0
+
+    def run(integrator, **over):
+        cfg = xf.config_from_workload(wl, integrator=integrator, **over)
+        cfg.cuda_stream = torch.cuda.current_stream().cuda_stream
+        s = xf.Solver(cfg)
+        s.set_spectra(wl.spectra())
+        s.reset(r0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        s.evolve(r0, r1)
+        e1.record()
+        torch.cuda.synchronize()
+        pee, _ = s.pee()
+        st = s.stats()
+        return pee, st, e0.elapsed_time(e1)
+
+    ref, _, _ = run("dp45", rtol=1e-12, atol=1e-12, h0_km=1e-3)
+    plan = [("exp_midpoint", dict(rtol=t, atol=t, h0_km=1e-3)) for t in (1e-4, 1e-5, 1e-6, 1e-7)]
+    plan += [("dp45", dict(rtol=t, atol=t, h0_km=1e-3)) for t in (1e-6, 1e-7, 1e-8, 1e-9, 1e-10)]
+    plan += [("lie_rk4", dict(fixed_dr_km=(r1 - r0) / n)) for n in (250, 500, 1000, 2000, 4000)]
+    plan += [("rk4", dict(fixed_dr_km=(r1 - r0) / n)) for n in (250, 500, 1000, 2000, 4000)]
+    for integ, over in plan:
+        pee, st, ms = run(integ, **over)
+        print(json.dumps({"integrator": integ, **{k: v for k, v in over.items() if k != "atol"},
+                          "max_abs_dpee": float(np.abs(pee - ref).max()), "stage_evals": int(st.stage_evals),
+                          "accepted": int(st.accepted), "rejected": int(st.rejected), "device_ms": ms,
+                          "workload": wl.name, "window_km": [r0, r1]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -218,7 +263,12 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--steps-per-launch", type=int, default=8,
                     help="radial steps per persistent launch in the timed region (L2 flushed before each)")
+    ap.add_argument("--compare-integrators", action="store_true",
+                    help="accuracy against cost of the integrators on the 4096-beam case instead of the benchmark")
     args = ap.parse_args()
+    if args.compare_integrators:
+        compare_integrators()
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -63,8 +63,14 @@ enum xflat_precision {
 enum xflat_integrator {
   XFLAT_RK4 = 0,              /* classical 4-stage RK on d(rho)/dr = -i[H,rho]/cos(theta), fixed step */
   XFLAT_DP45 = 1,             /* Dormand-Prince 5(4), FSAL, adaptive (error control below)        */
-  XFLAT_LIE_RK4 = 2           /* commutator-free Lie RK4 whose every update is an exact propagator
+  XFLAT_LIE_RK4 = 2,          /* commutator-free Lie RK4 whose every update is an exact propagator
                                  exp(-i H dl) of Eq. U (two flavours only), fixed step              */
+  XFLAT_EXP_MIDPOINT = 3      /* exponential midpoint rule (Lie-group Runge-Kutta-Munthe-Kaas method
+                                 with Runge's midpoint tableau; Sec. 3.4's exact propagator of Eq. U
+                                 with a mid-point scheme): y' = exp(-i H(r+h/2, y_half) dl) applied
+                                 to y, y_half from an exponential half step; the exponential Euler
+                                 step exp(-i H(r, y) dl) is the embedded first-order estimate
+                                 (error control as DP45 with the factor 0.9 Err^-1/2); two flavours */
 };
 enum xflat_matter {
   XFLAT_MATTER_NONE = 0,

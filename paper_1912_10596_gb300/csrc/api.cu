@@ -107,6 +107,8 @@ int fail(xflat_t h, int code, const std::string& msg) {
   } while (0)
 
 bool is_fin(double x) { return std::isfinite(x); }
+// integrators with embedded error control (adaptive step size)
+bool adaptive(uint32_t integrator) { return integrator == XFLAT_DP45 || integrator == XFLAT_EXP_MIDPOINT; }
 
 int check_config(const xflat_config& c, std::string& why) {
   if (c.abi_version != XFLAT_ABI_VERSION) { why = "abi_version mismatch"; return XFLAT_ERR_INVAL; }
@@ -116,14 +118,16 @@ int check_config(const xflat_config& c, std::string& why) {
   if (nb >= (1ull << 31)) { why = "too many beams in one instance"; return XFLAT_ERR_INVAL; }
   if (nb * (uint64_t)c.n_energy >= (1ull << 40)) { why = "n_beams * n_energy must be < 2^40"; return XFLAT_ERR_INVAL; }
   if (c.precision > 1) { why = "precision must be FP64 or MIXED"; return XFLAT_ERR_INVAL; }
-  if (c.integrator > 2) { why = "unknown integrator"; return XFLAT_ERR_INVAL; }
-  if (c.integrator == XFLAT_LIE_RK4 && c.n_flavor != 2) { why = "LIE_RK4 is two-flavour only"; return XFLAT_ERR_UNSUPPORTED; }
+  if (c.integrator > 3) { why = "unknown integrator"; return XFLAT_ERR_INVAL; }
+  if ((c.integrator == XFLAT_LIE_RK4 || c.integrator == XFLAT_EXP_MIDPOINT) && c.n_flavor != 2) {
+    why = "the exponential integrators are two-flavour only"; return XFLAT_ERR_UNSUPPORTED;
+  }
   if (c.matter_kind > 2) { why = "unknown matter_kind"; return XFLAT_ERR_INVAL; }
   if (!(c.R_km > 0) || !is_fin(c.R_km)) { why = "R_km must be > 0"; return XFLAT_ERR_INVAL; }
   if (!(c.E_min_MeV > 0) || !(c.E_max_MeV > c.E_min_MeV) || !is_fin(c.E_max_MeV)) { why = "need 0 < E_min < E_max"; return XFLAT_ERR_INVAL; }
   for (int i = 0; i < 2; ++i) if (!is_fin(c.dm2_eV2[i])) { why = "dm2 not finite"; return XFLAT_ERR_INVAL; }
   for (int i = 0; i < 3; ++i) if (!is_fin(c.theta[i])) { why = "theta not finite"; return XFLAT_ERR_INVAL; }
-  if (c.integrator == XFLAT_DP45) {
+  if (adaptive(c.integrator)) {
     if (!(c.rtol >= 0) || !(c.atol >= 0) || !(c.rtol + c.atol > 0)) { why = "need rtol, atol >= 0, not both 0"; return XFLAT_ERR_INVAL; }
     if (!(c.h0_km > 0) || !(c.h_min_km >= 0)) { why = "need h0 > 0 and h_min >= 0"; return XFLAT_ERR_INVAL; }
   } else if (!(c.fixed_dr_km > 0)) { why = "fixed-step integrators need fixed_dr_km > 0"; return XFLAT_ERR_INVAL; }
@@ -335,7 +339,7 @@ void fill_inst_const(HostInst& I, InstConst& ic) {
   ic.div_magic = (1ull << 40) / c.n_energy + 1;
   ic.R2 = c.R_km * c.R_km;
   ic.matter = (int)c.matter_kind;
-  ic.adaptive = c.integrator == XFLAT_DP45;
+  ic.adaptive = adaptive(c.integrator);
   ic.r_ref = c.r_ref_km > 0 ? c.r_ref_km : 1.0;
   ic.power = c.power;
   ic.lam_coef = c.matter_kind == XFLAT_MATTER_POWER_LAW ? kSqrt2GFhc2 * c.Ye * c.rho0_gcc / kMuG * 1e15 : 0.0;
@@ -387,7 +391,7 @@ void reset_dyn(xflat_t h, uint32_t i, double r0) {
   std::memset(&d, 0, sizeof(InstDyn));
   d.r = r0;
   d.r_end = r0;
-  d.h = c.integrator == XFLAT_DP45 ? c.h0_km : c.fixed_dr_km;
+  d.h = adaptive(c.integrator) ? c.h0_km : c.fixed_dr_km;
   d.done = 1;
 }
 
@@ -650,7 +654,7 @@ int do_evolve(xflat_t h, const double* r1, bool sync_loop, uint32_t max_steps, i
       changed = true;
       d.r_end = target;
       d.done = d.r >= target ? 1 : 0;
-      if (c.integrator != XFLAT_DP45) {
+      if (!adaptive(c.integrator)) {
         const double span = target - d.r;
         long long n = (long long)std::ceil(span / c.fixed_dr_km - 1e-9);
         if (n < 1) n = 1;
@@ -1106,7 +1110,7 @@ int xflat_get_stats_inst(xflat_t h, uint32_t inst, xflat_stats* out) {
   std::memset(out, 0, sizeof(*out));
   const InstDyn& d = h->dyn[inst];
   out->r_km = d.r;
-  out->h_km = h->inst[inst].cfg.integrator == XFLAT_DP45 ? d.h : d.h_fixed;
+  out->h_km = adaptive(h->inst[inst].cfg.integrator) ? d.h : d.h_fixed;
   out->last_err = d.err;
   out->accepted = d.accepted;
   out->rejected = d.rejected;

@@ -39,10 +39,18 @@ namespace xflat {
 
 // --------------------------------------------------------------------------------------------
 // Butcher tableaus (1-based stage indices).
+// Traits of every tableau: S stages (stage radii r + c_s h), kPasses passes per step,
+// kAdaptive (embedded error control), kErrPow (the controller's exponent is -1/kErrPow),
+// kFinalMoments (the final pass reduces the moments of the new state: stage 1 of the next step),
+// kEvalsPerStep (new stage evaluations per step), kEM2 (exponential midpoint rule).
 struct TabRK4 {
   static constexpr int S = 4;
   static constexpr int kPasses = 4;
   static constexpr bool kAdaptive = false;
+  static constexpr int kErrPow = 5;
+  static constexpr bool kFinalMoments = true;
+  static constexpr int kEvalsPerStep = 4;
+  static constexpr bool kEM2 = false;
   __host__ __device__ static constexpr double a(int i, int j) {
     return (i == 2 && j == 1) ? 0.5 : (i == 3 && j == 2) ? 0.5 : (i == 4 && j == 3) ? 1.0 : 0.0;
   }
@@ -60,6 +68,10 @@ struct TabDP45 {
   static constexpr int S = 7;
   static constexpr int kPasses = 7;
   static constexpr bool kAdaptive = true;
+  static constexpr int kErrPow = 5;
+  static constexpr bool kFinalMoments = false;   // first same as last: stage 7 is the new state
+  static constexpr int kEvalsPerStep = 6;
+  static constexpr bool kEM2 = false;
   __host__ __device__ static constexpr double a(int i, int j) {
     return i == 2 ? (j == 1 ? 1.0 / 5 : 0.0)
          : i == 3 ? (j == 1 ? 3.0 / 40 : j == 2 ? 9.0 / 40 : 0.0)
@@ -89,10 +101,32 @@ struct TabCF4 {
   static constexpr int S = 4;
   static constexpr int kPasses = 4;
   static constexpr bool kAdaptive = false;
+  static constexpr int kErrPow = 5;
+  static constexpr bool kFinalMoments = true;
+  static constexpr int kEvalsPerStep = 4;
+  static constexpr bool kEM2 = false;
   __host__ __device__ static constexpr double a(int, int) { return 0.0; }
   __host__ __device__ static constexpr double b(int) { return 0.0; }
   __host__ __device__ static constexpr double e(int) { return 0.0; }
   __host__ __device__ static constexpr double c(int i) { return TabRK4::c(i); }
+};
+
+// Exponential midpoint rule (Lie-group Runge-Kutta-Munthe-Kaas method with Runge's midpoint
+// tableau) with its exponential-Euler partner as the embedded first-order estimate: stage 1 at r
+// (generator K1), stage 2 at r + h/2 from the half step Y_half = exp(h/2 K1) y, the new state
+// exp(h K2) y, the estimate exp(h K1) y; stage 3 is the new state at r + h (the next step's stage 1).
+struct TabEM2 {
+  static constexpr int S = 3;
+  static constexpr int kPasses = 2;
+  static constexpr bool kAdaptive = true;
+  static constexpr int kErrPow = 2;
+  static constexpr bool kFinalMoments = true;
+  static constexpr int kEvalsPerStep = 2;
+  static constexpr bool kEM2 = true;
+  __host__ __device__ static constexpr double a(int, int) { return 0.0; }
+  __host__ __device__ static constexpr double b(int) { return 0.0; }
+  __host__ __device__ static constexpr double e(int) { return 0.0; }
+  __host__ __device__ static constexpr double c(int i) { return i == 1 ? 0.0 : (i == 2 ? 0.5 : 1.0); }
 };
 
 // Largest finite value of the working precision.
@@ -401,20 +435,23 @@ __device__ __forceinline__ double stage_c(int i) { return Tab::c(i); }
 // The last block to arrive: reduce accumulators, derive stage constants, run the controller.
 // Every value another block may have written since this SM last looked is read through L2
 // (__ldcg), never from a possibly stale L1 line; the loads are issued before any branch on them.
-// 0.9 Err^(-1/5), the unclamped step-size factor, in double.  The caller clamps it to [0.2, 5],
-// which decides alone below Err = (0.9/5)^5 = 1.8896e-4 and above (0.9/0.2)^5 = 1845.3, so only
-// (a slightly wider) range is computed: a float seed refined by two Newton steps for y^-5 = Err,
-// y <- y (1.2 - 0.2 Err y^5), which need no division (one FP64 pow costs ~5800 cycles of latency
-// on this part, the two steps ~800) and converge to double accuracy.
+// 0.9 Err^(-1/P), the unclamped step-size factor, in double (P = 5 for the 5(4) pair, 2 for the
+// 2(1) pair).  The caller clamps it to [0.2, 5], which decides alone below Err = (0.9/5)^P and
+// above (0.9/0.2)^P, so only (a slightly wider) range is computed: a float seed refined by two
+// Newton steps for y^-P = Err, y <- y ((P + 1) - Err y^P) / P, which need no division (one FP64
+// pow costs ~5800 cycles of latency on this part, the two steps ~800) and converge to double
+// accuracy.
+template <int P>
 __device__ __forceinline__ double controller_factor(double err) {
-  if (!(err > 1.5e-4)) return 5.0;
-  if (!(err < 2000.0)) return 0.0;
-  double y = (double)powf((float)err, -0.2f);
-#pragma unroll
+  constexpr double lo = P == 5 ? 1.5e-4 : 0.025, hi = P == 5 ? 2000.0 : 25.0;
+  if (!(err > lo)) return 5.0;
+  if (!(err < hi)) return 0.0;
+  double y = (double)powf((float)err, -1.0f / (float)P);
   for (int it = 0; it < 2; ++it) {
-    const double y2 = y * y;
-    const double y5 = y2 * y2 * y;
-    y = y * fma(-0.2 * err, y5, 1.2);
+    double yp = y;
+#pragma unroll
+    for (int q = 1; q < P; ++q) yp *= y;
+    y = y * fma(-err / P, yp, (P + 1.0) / P);
   }
   return 0.9 * y;
 }
@@ -482,8 +519,8 @@ __device__ int serial_update(const KParams& p, int slot, bool final_pass, bool i
     const InstConst& ic = p.ic[i];
     InstDyn& d = p.dyn[i];
     const unsigned long long* acc = p.acc + (size_t)i * kAccWordsPerInst + (size_t)slot * kAccCopies * kNMMax * 2;
-    const bool have_moments = !(final_pass && Tab::kAdaptive);
-    const bool adaptive_final = final_pass && Tab::kAdaptive;
+    const bool have_moments = !(final_pass && !Tab::kFinalMoments);
+    const bool adaptive_final = final_pass && Tab::kAdaptive && !Tab::kFinalMoments;   // FSAL
     // ---- every load first (no store may sit between them) -------------------------------
     const int done = __ldcg(&d.done), status = __ldcg(&d.status), nonfin = __ldcg(&p.nonfinite[i]);
     const unsigned long long eb = __ldcg(&p.errmax[i]);
@@ -535,7 +572,7 @@ __device__ int serial_update(const KParams& p, int slot, bool final_pass, bool i
     } else if (!Tab::kAdaptive) {
       parity ^= 1;
       accepted += 1;
-      evals += 4;
+      evals += Tab::kEvalsPerStep;
       nfix += 1;
       fin = nfix >= nfix_tot;
       r = fin ? r_end : r0f + (double)nfix * hf;
@@ -551,15 +588,25 @@ __device__ int serial_update(const KParams& p, int slot, bool final_pass, bool i
       const double err = __longlong_as_double((long long)eb);
       p.errmax[i] = 0ull;
       d.err = err;
-      evals += 6;
+      evals += Tab::kEvalsPerStep;
       const bool ok = err <= 1.0;
-      const double q = controller_factor(err);
+      const double q = controller_factor<Tab::kErrPow>(err);
       if (ok) {
         r = last ? r_end : r + hh;
         parity ^= 1;
         accepted += 1;
-        for (int c = 0; c < NM; ++c) d.mom[1][c] = m7[c];
-        for (int c = 0; c < Phys::NSC; ++c) d.sc[1][c] = sc7[c];
+        if (Tab::kFinalMoments) {
+          // the final pass reduced the new state's moments at r + h: stage 1 of the next step
+          for (int c = 0; c < NM; ++c) d.mom[1][c] = m[c];
+          for (int c = 0; c < NCOMP; ++c) {
+            d.sc[1][c] = mu * m[c];
+            d.sc[1][NCOMP + c] = mu * m[NCOMP + c];
+          }
+          d.sc[1][NM] = lam;
+        } else {
+          for (int c = 0; c < NM; ++c) d.mom[1][c] = m7[c];
+          for (int c = 0; c < Phys::NSC; ++c) d.sc[1][c] = sc7[c];
+        }
         fin = last != 0;
       } else {
         rejected += 1;
@@ -596,6 +643,20 @@ __device__ int serial_update(const KParams& p, int slot, bool final_pass, bool i
     if (!fin && !step_err) all_finished = 0;
   }
   return all_finished;
+}
+
+// Accumulator slots of the stages kPasses..S (no pass of their own index clears them), zeroed by
+// the last block of the final barrier: nobody accumulates into or reads them until the next step
+// (the fence in serial_geometry publishes the stores before the release).
+template <class Tab>
+__device__ void clear_late_slots(const KParams& p) {
+  constexpr int kWords = kAccCopies * kNMMax * 2;
+  constexpr int kLate = Tab::S - Tab::kPasses + 1;
+  for (int t = threadIdx.x; t < p.n_inst * kLate * kWords; t += blockDim.x) {
+    const int inst = t / (kLate * kWords), rem = t % (kLate * kWords);
+    const int slot = Tab::kPasses + rem / kWords;
+    p.acc[(size_t)inst * kAccWordsPerInst + (size_t)slot * kWords + rem % kWords] = 0ull;
+  }
 }
 
 // The next step's stage radii, R^2/r^2, mu and lambda, one (instance, stage) per thread of the last
@@ -719,7 +780,9 @@ enum PassKind : int { kStagePass = 0, kFinalPass = 1, kInitPass = 2 };
 // pipe.  FP32 kernels rebuild the chain in the final pass instead: their state, y5 and those
 // partials together exceed the L2, and the extra DRAM traffic costs more than the FP32 chain.
 template <class Tab, typename Real>
-__host__ __device__ constexpr bool split_final() { return Tab::kAdaptive && sizeof(Real) == 8; }
+__host__ __device__ constexpr bool split_final() {
+  return Tab::kAdaptive && !Tab::kFinalMoments && !Tab::kEM2 && sizeof(Real) == 8;   // DP45 in FP64
+}
 
 template <class Phys, class Tab, typename Real, bool kCF, int kPass, int kKind>
 struct PassBody;
@@ -884,6 +947,40 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
       return;
     }
     const Real h = bs.hB[0];
+    if constexpr (Tab::kEM2) {
+      // exponential midpoint rule: half step with K1 -> Y_half (moments at r + h/2); final pass:
+      // y' = exp(h K2) y, the estimate exp(h K1) y, the error ratio, moments of y' at r + h
+      Real K1[3], Om[3];
+      Phys::K(tv.row(1, tj), bm, bs.vac, bs.scr[1], K1);
+      if (kKind == kStagePass) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Om[i] = Real(0.5) * h * K1[i];
+        rotate(Om, y);
+        Phys::accum(acc, bm.w, Phys::t1(tv.row(2, tj)), y);
+        return;
+      }
+      Real K2[3], yn[3], ye[3], e[3];
+      Phys::K(tv.row(2, tj), bm, bs.vac, bs.scr[2], K2);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { yn[i] = y[i]; ye[i] = y[i]; Om[i] = h * K2[i]; }
+      rotate(Om, yn);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) Om[i] = h * K1[i];
+      rotate(Om, ye);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) e[i] = yn[i] - ye[i];
+      if (!(Phys::tnorm2(y) <= rbig<Real>())) bad = 1;       // non-finite input state: fatal
+      const bool ynok = Phys::tnorm2(yn) <= rbig<Real>();
+      const Real den = bs.atol + bs.rtol * sqrt(fmax(Phys::tnorm2(y), Phys::tnorm2(yn)));
+      Real r2 = Phys::tnorm2(e) / (den * den);
+      if (!(r2 <= rbig<Real>()) || !ynok) r2 = Real(INFINITY);
+      emax = fmax(emax, r2);
+      if (mixed && ynok) Phys::normalise(yn);
+      Phys::accum(acc, bm.w, Phys::t1(tv.row(3, tj)), yn);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) y[i] = yn[i];
+      return;
+    }
     Real K1[3], K2[3], K3[3], K4[3], Om[3];
     Phys::K(tv.row(1, tj), bm, bs.vac, bs.scr[1], K1);
     if (kKind == kStagePass && kPass == 0) {
@@ -1162,17 +1259,20 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
   const bool mixed = sizeof(Real) == 4;
   const int slot = kKind == kInitPass ? 1 : (kKind == kStagePass ? kPass + 2 : 0);
   // Clear accumulator slots nobody reads any more (block 0, while the other blocks already work).
-  // Stage s (2 <= s <= S) is reduced in pass s - 2 and read by every block in the set-up of pass
-  // s - 1, so it is cleared at the start of pass s (stage S: at the start of the next step's pass
-  // 0, with the final pass's slot 0 and the moment launch's slot 1, both read by serial updates
-  // that finish before their barrier opens).  Nothing accumulates into a cleared slot until at
-  // least one barrier later, and block 0's stores are fenced at its next arrival.
+  // Stage s (2 <= s < kPasses) is reduced in pass s - 2 and read by every block in the set-up of
+  // pass s - 1, so it is cleared at the start of pass s; pass 0 clears the final pass's slot 0 and
+  // the moment launch's slot 1, both read by serial updates that finish before their barrier
+  // opens.  Stages with no pass of their own index (kPasses <= s <= S: stage S of RK4 / DP45,
+  // stages 2 and 3 of the exponential midpoint rule) are cleared by the final pass's serial section
+  // (clear_late_slots) while every other block waits at the final barrier.  Nothing accumulates
+  // into a cleared slot until at least one barrier later, and block 0's stores are fenced at its
+  // next arrival.
   if (kKind != kInitPass && blockIdx.x == 0) {
     constexpr int kWords = kAccCopies * kNMMax * 2;
-    constexpr int kSlots = kPass == 0 ? 3 : (kPass >= 2 ? 1 : 0);
+    constexpr int kSlots = kPass == 0 ? 2 : (kPass >= 2 ? 1 : 0);
     for (int t = threadIdx.x; t < p.n_inst * kSlots * kWords; t += blockDim.x) {
       const int inst = t / (kSlots * kWords), rem = t % (kSlots * kWords), q = rem / kWords;
-      const int zslot = kPass == 0 ? (q == 0 ? 0 : (q == 1 ? 1 : Tab::S)) : kPass;
+      const int zslot = kPass == 0 ? q : kPass;
       p.acc[(size_t)inst * kAccWordsPerInst + (size_t)zslot * kWords + rem % kWords] = 0ull;
     }
   }
@@ -1435,14 +1535,19 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       const int any_bad = __syncthreads_or(bad);
       if (any_bad && threadIdx.x == 0) atomicExch(&p.nonfinite[pc.inst], 1);
     }
-    // reduce this piece into the instance accumulators
+    // reduce this piece into the instance accumulators: the error maximum (final pass of an
+    // adaptive tableau) and the moments (every pass but a final one without moments); a
+    // non-finite moment rejects an adaptive trial step and is fatal for a fixed step
+    constexpr bool kErrMax = kKind == kFinalPass && Tab::kAdaptive;
+    constexpr bool kMoments = kKind != kFinalPass || Tab::kFinalMoments;
+    constexpr bool kRejectOverflow = Tab::kAdaptive;
     if constexpr (sizeof(Real) == 4) {
       // mixed precision: warp trees in FP32, the warps' partials summed in a fixed order, and the
       // block's partial added to one of the instance's accumulator copies as a fixed-point integer
       // (integer atomics: order-independent; no FP64 instruction)
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
       float* redf = reinterpret_cast<float*>(red);
-      if (kKind == kFinalPass && Tab::kAdaptive) {
+      if constexpr (kErrMax) {
         float em = (emax <= 3.0e38f) ? (float)emax : INFINITY;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) em = fmaxf(em, __shfl_down_sync(0xffffffffu, em, o));
@@ -1455,7 +1560,9 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
           // the beams gave squared error ratios
           atomicMax(&p.errmax[pc.inst], (unsigned long long)__double_as_longlong(sqrt((double)m)));
         }
-      } else {
+      }
+      if constexpr (kMoments) {
+        if constexpr (kErrMax) __syncthreads();              // the scratch is reused
 #pragma unroll
         for (int i = 0; i < NM; ++i)
 #pragma unroll
@@ -1473,45 +1580,47 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
                                   (((size_t)slot * kAccCopies + blockIdx.x % kAccCopies) * kNMMax + threadIdx.x) * 2;
           if (f32_to_fix48(sum, fx)) {
             atomicAdd(a, (unsigned long long)fx);
-          } else if (Tab::kAdaptive && kKind == kStagePass) {
+          } else if (kRejectOverflow) {
             atomicMax(&p.errmax[pc.inst], 0x7ff0000000000000ull);   // overflowing trial step
           } else {
             atomicExch(&p.nonfinite[pc.inst], 1);
           }
         }
       }
-    } else if (kKind == kFinalPass && Tab::kAdaptive) {
-      const double em = (emax <= rbig<Real>()) ? (double)emax : __longlong_as_double(0x7ff0000000000000ll);
-      const int any_bad = __syncthreads_or(bad);
-      const double bmax = block_max(em, red);
-      if (threadIdx.x == 0) {
-        if (any_bad) atomicExch(&p.nonfinite[pc.inst], 1);
-        // the beams gave squared error ratios
-        atomicMax(&p.errmax[pc.inst], (unsigned long long)__double_as_longlong(sqrt(bmax)));
-      }
     } else {
-      double v[NM];
-#pragma unroll
-      for (int i = 0; i < NM; ++i) v[i] = (double)acc[i];
-      block_sum<NM>(v, red);
-      if (threadIdx.x == 0) {
-        bool fin = true;
-#pragma unroll
-        for (int i = 0; i < NM; ++i) { bs.fx[i] = v[i]; fin = fin && (fabs(v[i]) <= 1.7e308); }
-        bs.flag = fin ? 1 : 0;
-        if (!fin) {
-          // adaptive: an overflowing trial step is rejected by the controller; fixed step: fatal
-          if (Tab::kAdaptive && kKind == kStagePass)
-            atomicMax(&p.errmax[pc.inst], 0x7ff0000000000000ull);
-          else
-            atomicExch(&p.nonfinite[pc.inst], 1);
+      if constexpr (kErrMax) {
+        const double em = (emax <= rbig<Real>()) ? (double)emax : __longlong_as_double(0x7ff0000000000000ll);
+        const int any_bad = __syncthreads_or(bad);
+        const double bmax = block_max(em, red);
+        if (threadIdx.x == 0) {
+          if (any_bad) atomicExch(&p.nonfinite[pc.inst], 1);
+          // the beams gave squared error ratios
+          atomicMax(&p.errmax[pc.inst], (unsigned long long)__double_as_longlong(sqrt(bmax)));
         }
       }
-      __syncthreads();
-      if (bs.flag && threadIdx.x < NM) {
-        unsigned long long* a = p.acc + (size_t)pc.inst * kAccWordsPerInst +
-                                (((size_t)slot * kAccCopies + blockIdx.x % kAccCopies) * kNMMax + threadIdx.x) * 2;
-        fx_add(a, bs.fx[threadIdx.x]);
+      if constexpr (kMoments) {
+        double v[NM];
+#pragma unroll
+        for (int i = 0; i < NM; ++i) v[i] = (double)acc[i];
+        block_sum<NM>(v, red);
+        if (threadIdx.x == 0) {
+          bool fin = true;
+#pragma unroll
+          for (int i = 0; i < NM; ++i) { bs.fx[i] = v[i]; fin = fin && (fabs(v[i]) <= 1.7e308); }
+          bs.flag = fin ? 1 : 0;
+          if (!fin) {
+            if (kRejectOverflow)
+              atomicMax(&p.errmax[pc.inst], 0x7ff0000000000000ull);
+            else
+              atomicExch(&p.nonfinite[pc.inst], 1);
+          }
+        }
+        __syncthreads();
+        if (bs.flag && threadIdx.x < NM) {
+          unsigned long long* a = p.acc + (size_t)pc.inst * kAccWordsPerInst +
+                                  (((size_t)slot * kAccCopies + blockIdx.x % kAccCopies) * kNMMax + threadIdx.x) * 2;
+          fx_add(a, bs.fx[threadIdx.x]);
+        }
       }
     }
   }
@@ -1549,6 +1658,7 @@ __device__ __forceinline__ bool pass_and_sync(const KParams& p, BlockShared<Real
   } else if ((res & 0xf) == kBarLast) {
     const int mine = serial_update<Phys, Tab, Real>(p, 0, true, false);
     const int all = __syncthreads_and(mine);
+    clear_late_slots<Tab>(p);
     serial_geometry<Tab>(p);
     if (threadIdx.x == 0) {
       *p.all_done = all;

@@ -27,7 +27,7 @@ constexpr int kAccCopies = 8;
 // accumulator words per instance: [stage slot][copy][component][2]
 constexpr int kAccWordsPerInst = kMaxStages * kAccCopies * kNMMax * 2;
 
-enum Integrator : int { kRK4 = 0, kDP45 = 1, kLieRK4 = 2 };
+enum Integrator : int { kRK4 = 0, kDP45 = 1, kLieRK4 = 2, kExpMid = 3 };
 enum Matter : int { kMatterNone = 0, kMatterPower = 1, kMatterConst = 2 };
 
 // Instance constants, written by the host before a launch.

@@ -59,3 +59,8 @@ def test_create_rejects_bad_config_before_touching_the_gpu(lib_path):
     c.integrator = xflat.LIE_RK4
     c.n_flavor = 3
     assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_UNSUPPORTED
+    c.integrator = xflat.EXP_MIDPOINT
+    assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_UNSUPPORTED
+    c = xflat.default_config()
+    c.integrator = 4
+    assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_INVAL
