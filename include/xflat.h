@@ -96,7 +96,11 @@ typedef struct {
   uint32_t precision;         /* xflat_precision                                                   */
   uint32_t integrator;        /* xflat_integrator                                                  */
   uint32_t matter_kind;       /* xflat_matter                                                      */
-  uint32_t reserved0;
+  uint32_t n_phi;             /* 0 or 1: bulb model; >= 2: extended bulb model (Sec. 2, Eq. int-v)
+                                 with n_phi equal azimuthal bins phi_p = 2 pi (p + 1/2) / n_phi
+                                 around the radial direction, two flavours only.  Beams are then
+                                 indexed with a combined angle bin a = j n_phi + p in place of j
+                                 (weight du_j / n_phi), n_beams = 2 n_angle n_phi n_energy.       */
   double R_km;                /* neutrino-sphere radius R                                          */
   double E_min_MeV, E_max_MeV;/* energy range, bins of equal width, midpoints                      */
   double dm2_eV2[2];          /* 2 flavours: dm2[0]; 3 flavours: dm2_21, dm2_31 (signed)          */
@@ -208,6 +212,12 @@ int xflat_advance_graph(xflat_t h, uint32_t n_launches, uint32_t max_steps, int*
  * row major), units of 1/s.  Computed by the device reduction (deterministic order). */
 int xflat_moments(xflat_t h, double* J0, double* J1);
 int xflat_moments_inst(xflat_t h, uint32_t inst, double* J0, double* J1);
+
+/* Extended bulb model (n_phi >= 2): the azimuthal moments of the current state,
+ *   Jc = sum_b du_a F_b (sin th_b / cos th_b) cos phi_b,   Js = the same with sin phi_b
+ * (Eq. F: Phi_sc = R^2/(2 r^2) Jc, Phi_ss = R^2/(2 r^2) Js with the 1/2pi of Eq. int-v), traceless
+ * parts, 2 n^2 doubles each as J0 and J1.  XFLAT_ERR_UNSUPPORTED for the bulb model. */
+int xflat_moments_phi(xflat_t h, uint32_t inst, double* Jc, double* Js);
 
 /* Copy the state of instance 0 (inst: instance inst) out in the given layout (double).  dst is a
  * host pointer (dst_is_device = 0) or a device pointer on the handle's device (1) holding

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxflat.so")
-SOURCES = ["api.cu", "kernels_2f.cu", "kernels_3f.cu", "adjoint_2f.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "kernels_2f.cu", "kernels_2e.cu", "kernels_3f.cu", "adjoint_2f.cu", "noalloc.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-diag-suppress", "128",
               "-Xptxas", "-v"]

@@ -29,7 +29,7 @@ const double kSqrt2GFhc2 = std::sqrt(2.0) * kGF * kHbarcGevKm * kHbarcGevKm;
 
 constexpr uint32_t kMaxJJ = 128;          // combined angle bins per piece (shared-memory table rows)
 constexpr uint32_t kAlignBeams = 4;       // instance offsets and piece starts: 16-byte vectors
-uint32_t max_jj_cap(int nf, size_t real_size);
+uint32_t max_jj_cap(int nf, size_t real_size, bool ext = false);
 
 struct HostInst {
   xflat_config cfg;
@@ -46,6 +46,7 @@ struct HostInst {
 struct xflat_s {
   std::vector<HostInst> inst;
   int nf = 2, precision = 0, integrator = 0;
+  bool extended = false;                   // extended bulb model (azimuthal bins)
   size_t real_size = 8;
   int nc = 3;
   cudaStream_t stream = nullptr;
@@ -107,6 +108,8 @@ int fail(xflat_t h, int code, const std::string& msg) {
   } while (0)
 
 bool is_fin(double x) { return std::isfinite(x); }
+// combined angle bins (u x phi) of an instance: n_angle, times n_phi for the extended bulb model
+uint32_t angle_bins(const xflat_config& c) { return c.n_angle * (c.n_phi >= 2 ? c.n_phi : 1u); }
 // integrators with embedded error control (adaptive step size)
 bool adaptive(uint32_t integrator) { return integrator == XFLAT_DP45 || integrator == XFLAT_EXP_MIDPOINT; }
 
@@ -114,7 +117,9 @@ int check_config(const xflat_config& c, std::string& why) {
   if (c.abi_version != XFLAT_ABI_VERSION) { why = "abi_version mismatch"; return XFLAT_ERR_INVAL; }
   if (c.n_flavor != 2 && c.n_flavor != 3) { why = "n_flavor must be 2 or 3"; return XFLAT_ERR_INVAL; }
   if (c.n_energy < 1 || c.n_angle < 1) { why = "n_energy and n_angle must be >= 1"; return XFLAT_ERR_INVAL; }
-  const uint64_t nb = 2ull * c.n_energy * c.n_angle;
+  if (c.n_phi >= 2 && c.n_flavor != 2) { why = "the extended bulb model is two-flavour only"; return XFLAT_ERR_UNSUPPORTED; }
+  if (c.n_phi > 4096) { why = "n_phi must be <= 4096"; return XFLAT_ERR_INVAL; }
+  const uint64_t nb = 2ull * c.n_energy * c.n_angle * (c.n_phi >= 2 ? c.n_phi : 1u);
   if (nb >= (1ull << 31)) { why = "too many beams in one instance"; return XFLAT_ERR_INVAL; }
   if (nb * (uint64_t)c.n_energy >= (1ull << 40)) { why = "n_beams * n_energy must be < 2^40"; return XFLAT_ERR_INVAL; }
   if (c.precision > 1) { why = "precision must be FP64 or MIXED"; return XFLAT_ERR_INVAL; }
@@ -333,7 +338,8 @@ void fill_inst_const(HostInst& I, InstConst& ic) {
   ic.beam_off = I.off;
   ic.n_beams = I.n_beams;
   ic.n_energy = c.n_energy;
-  ic.n_angle = c.n_angle;
+  ic.n_angle = angle_bins(c);
+  ic.n_phi = c.n_phi >= 2 ? c.n_phi : 1u;
   ic.e_off = I.e_off;
   ic.a_off = I.a_off;
   ic.div_magic = (1ull << 40) / c.n_energy + 1;
@@ -411,7 +417,7 @@ void build_pieces(xflat_t h, int G) {
       const uint64_t lo = std::max<uint64_t>(s0, I.off), hi = std::min<uint64_t>(s1, I.off + I.n_beams);
       if (lo >= hi) continue;
       const uint32_t ne = I.cfg.n_energy;
-      const uint64_t maxlen = std::max<uint64_t>(kAlignBeams, ((uint64_t)(max_jj_cap(h->nf, h->real_size) - 1) * ne) / kAlignBeams * kAlignBeams);
+      const uint64_t maxlen = std::max<uint64_t>(kAlignBeams, ((uint64_t)(max_jj_cap(h->nf, h->real_size, h->extended) - 1) * ne) / kAlignBeams * kAlignBeams);
       for (uint64_t a = lo; a < hi; a += maxlen) {
         const uint64_t e = std::min<uint64_t>(hi, a + maxlen);
         Piece p{};
@@ -430,12 +436,16 @@ void build_pieces(xflat_t h, int G) {
 
 // Values per (stage, angle bin) table row of the step kernel (Phys2<float>::KT, Phys2<double>::KT,
 // Phys3::KT), and the cap on angle bins per piece that bounds the table's shared memory.
-int table_row_values(int nf, size_t real_size) { return nf == 2 ? (real_size == 4 ? 24 : 8) : 4; }
-uint32_t max_jj_cap(int nf, size_t real_size) { return (nf == 2 && real_size == 4) ? 64u : kMaxJJ; }
+int table_row_values(int nf, size_t real_size, bool ext = false) {
+  return ext ? 10 : (nf == 2 ? (real_size == 4 ? 24 : 8) : 4);
+}
+uint32_t max_jj_cap(int nf, size_t real_size, bool ext) {
+  return (nf == 2 && real_size == 4 && !ext) ? 64u : kMaxJJ;
+}
 
-size_t smem_bytes(int nf, size_t real_size, int max_jj) {
+size_t smem_bytes(int nf, size_t real_size, int max_jj, bool ext = false) {
   size_t s = 32 * kNMMax * sizeof(double);
-  s += (size_t)kMaxStages * max_jj * table_row_values(nf, real_size) * real_size;
+  s += (size_t)kMaxStages * max_jj * table_row_values(nf, real_size, ext) * real_size;
   s += (size_t)max_jj * real_size;                 // angle weights
   s = (s + 7) / 8 * 8 + (size_t)max_jj * sizeof(double);   // angle positions
   return (s + 15) / 16 * 16;
@@ -591,9 +601,10 @@ int setup_launch_shape(xflat_t h, const xflat_config& c) {
   // is built for one 256-thread block per SM.  Default: 256 threads x 3 blocks.
   h->block = c.block_size ? (int)c.block_size : 256;
   const int want_bps = c.blocks_per_sm ? (int)c.blocks_per_sm : (768 / h->block);
-  h->kernel = step_kernel_ptr(h->nf, h->precision, h->integrator, h->block, want_bps * h->block >= 768 ? 3 : 2);
+  h->kernel = step_kernel_ptr(h->nf, h->precision, h->integrator, h->block, want_bps * h->block >= 768 ? 3 : 2,
+                              h->extended);
   if (!h->kernel) return fail(h, XFLAT_ERR_UNSUPPORTED, "no kernel for this flavour/precision/integrator");
-  const size_t smax = smem_bytes(h->nf, h->real_size, max_jj_cap(h->nf, h->real_size));
+  const size_t smax = smem_bytes(h->nf, h->real_size, max_jj_cap(h->nf, h->real_size, h->extended), h->extended);
   CUDA_TRY(h, cudaFuncSetAttribute(h->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
   int occ = 0;
   CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h->kernel, h->block, smax));
@@ -607,7 +618,7 @@ int setup_launch_shape(xflat_t h, const xflat_config& c) {
   G = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)G, (T + per_block - 1) / per_block));
   h->grid = G;
   build_pieces(h, G);
-  h->smem = smem_bytes(h->nf, h->real_size, h->max_jj);
+  h->smem = smem_bytes(h->nf, h->real_size, h->max_jj, h->extended);
   CUDA_TRY(h, cudaMalloc(&h->d_pieces, sizeof(Piece) * std::max<size_t>(1, h->pieces.size())));
   CUDA_TRY(h, cudaMalloc(&h->d_blk, sizeof(int) * h->blk.size()));
   CUDA_TRY(h, cudaMemcpy(h->d_pieces, h->pieces.data(), sizeof(Piece) * h->pieces.size(), cudaMemcpyHostToDevice));
@@ -709,13 +720,14 @@ int create_impl(const xflat_config* cfgs, uint32_t n, xflat_t* out) {
     int rc = check_config(cfgs[i], why);
     if (rc) { (void)why; return rc; }
     if (cfgs[i].n_flavor != cfgs[0].n_flavor || cfgs[i].precision != cfgs[0].precision ||
-        cfgs[i].integrator != cfgs[0].integrator)
+        cfgs[i].integrator != cfgs[0].integrator || (cfgs[i].n_phi >= 2) != (cfgs[0].n_phi >= 2))
       return XFLAT_ERR_INVAL;
   }
   xflat_t h = new (std::nothrow) xflat_s();
   if (!h) return XFLAT_ERR_NOMEM;
   auto bail = [&](int rc) { xflat_destroy(h); return rc; };
   h->nf = (int)cfgs[0].n_flavor;
+  h->extended = cfgs[0].n_phi >= 2;
   h->precision = (int)cfgs[0].precision;
   h->integrator = (int)cfgs[0].integrator;
   h->real_size = h->precision == XFLAT_FP64 ? 8 : 4;
@@ -735,19 +747,22 @@ int create_impl(const xflat_config* cfgs, uint32_t n, xflat_t* out) {
   for (uint32_t i = 0; i < n; ++i) {
     HostInst& I = h->inst[i];
     I.cfg = cfgs[i];
-    I.n_beams = 2u * I.cfg.n_energy * I.cfg.n_angle;
+    const uint32_t na_tot = angle_bins(I.cfg), nphi = I.cfg.n_phi >= 2 ? I.cfg.n_phi : 1u;
+    I.n_beams = 2u * I.cfg.n_energy * na_tot;
     I.n_pad = (I.n_beams + kAlignBeams - 1) / kAlignBeams * kAlignBeams;
     I.off = off;
     off += I.n_pad;
     I.e_off = eoff;
     eoff += (h->nf == 2 ? 3 : 4) * I.cfg.n_energy;
     I.a_off = aoff;
-    aoff += I.cfg.n_angle;
-    I.u.resize(I.cfg.n_angle);
-    I.du.resize(I.cfg.n_angle);
-    for (uint32_t j = 0; j < I.cfg.n_angle; ++j) {
-      I.u[j] = (j + 0.5) / I.cfg.n_angle;
-      I.du[j] = 1.0 / I.cfg.n_angle;
+    aoff += na_tot;
+    // combined angle bins a = j n_phi + p: u_j and du_j / n_phi (the azimuthal measure dphi / 2 pi)
+    I.u.resize(na_tot);
+    I.du.resize(na_tot);
+    for (uint32_t a = 0; a < na_tot; ++a) {
+      const uint32_t j = a / nphi;
+      I.u[a] = (j + 0.5) / I.cfg.n_angle;
+      I.du[a] = 1.0 / I.cfg.n_angle / nphi;
     }
     I.N.assign(2ull * h->nf * I.cfg.n_energy, 0.0);
   }
@@ -864,8 +879,11 @@ int xflat_set_spectra_inst(xflat_t h, uint32_t inst, const double* nnu, const do
       if (!(u_bins[j] >= 0.0 && u_bins[j] < 1.0)) return fail(h, XFLAT_ERR_INVAL, "u outside [0, 1)");
       if (!is_fin(u_weights[j]) || u_weights[j] < 0) return fail(h, XFLAT_ERR_INVAL, "bad u weight");
     }
-    I.u.assign(u_bins, u_bins + na);
-    I.du.assign(u_weights, u_weights + na);
+    const uint32_t nphi = I.cfg.n_phi >= 2 ? I.cfg.n_phi : 1u;
+    for (uint32_t a = 0; a < na * nphi; ++a) {
+      I.u[a] = u_bins[a / nphi];
+      I.du[a] = u_weights[a / nphi] / nphi;
+    }
   }
   I.N = N;
   I.spectra = true;
@@ -985,6 +1003,27 @@ int xflat_moments_inst(xflat_t h, uint32_t inst, double* J0, double* J1) {
 
 int xflat_moments(xflat_t h, double* J0, double* J1) { return xflat_moments_inst(h, 0, J0, J1); }
 
+int xflat_moments_phi(xflat_t h, uint32_t inst, double* Jc, double* Js) {
+  if (!h || !Jc || !Js) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
+  if (!h->extended) return fail(h, XFLAT_ERR_UNSUPPORTED, "azimuthal moments need the extended bulb model");
+  if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
+  if (!h->inst[inst].spectra) return fail(h, XFLAT_ERR_STATE, "set_spectra first");
+  int rc;
+  if ((rc = download_dyn(h))) return rc;
+  if (!h->moments_valid && (rc = refresh_moments(h))) return rc;
+  const InstDyn& d = h->dyn[inst];
+  const double ws = h->ic[inst].wscale;
+  for (int t = 0; t < 2; ++t) {
+    const double* m = &d.mom[1][6 + 3 * t];
+    double* J = t == 0 ? Jc : Js;
+    J[0] = 0.5 * ws * m[2];  J[1] = 0;
+    J[2] = 0.5 * ws * m[0];  J[3] = -0.5 * ws * m[1];
+    J[4] = 0.5 * ws * m[0];  J[5] = 0.5 * ws * m[1];
+    J[6] = -0.5 * ws * m[2]; J[7] = 0;
+  }
+  return XFLAT_OK;
+}
+
 int xflat_get_rho_inst(xflat_t h, uint32_t inst, void* dst, int dst_is_device, int layout) {
   if (!h || !dst) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
   if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
@@ -1055,7 +1094,7 @@ int xflat_pee_inst(xflat_t h, uint32_t inst, double* pee_per_beam, double* pee_m
   int rc;
   if ((rc = download_dyn(h))) return rc;
   const HostInst& I = h->inst[inst];
-  const uint32_t n = I.n_beams, ne = I.cfg.n_energy, na = I.cfg.n_angle;
+  const uint32_t n = I.n_beams, ne = I.cfg.n_energy, na = angle_bins(I.cfg);
   const size_t need = ((size_t)n + ne + 2) * 8;
   if ((rc = ensure_stage(h, need))) return rc;
   double* pee = h->d_stage;
@@ -1085,7 +1124,7 @@ int xflat_flux_spectra(xflat_t h, uint32_t inst, double* flux) {
   int rc;
   if ((rc = download_dyn(h))) return rc;
   const HostInst& I = h->inst[inst];
-  const uint32_t ne = I.cfg.n_energy, na = I.cfg.n_angle;
+  const uint32_t ne = I.cfg.n_energy, na = angle_bins(I.cfg);
   const int nf = h->nf;
   const size_t nval = 2ull * nf * ne;
   if ((rc = ensure_stage(h, 2 * nval * sizeof(double)))) return rc;
@@ -1132,8 +1171,8 @@ int xflat_get_stats(xflat_t h, xflat_stats* out) { return xflat_get_stats_inst(h
 int xflat_adjoint(xflat_t h, double r0_km, double r1_km, uint32_t n_steps, uint32_t checkpoint_every,
                   double* dJ_dN, double* dJ_dtheta, double* J_out) {
   if (!h) return XFLAT_ERR_INVAL;
-  if (h->nf != 2 || h->inst.size() != 1)
-    return fail(h, XFLAT_ERR_UNSUPPORTED, "the adjoint is built for one two-flavour instance");
+  if (h->nf != 2 || h->inst.size() != 1 || h->extended)
+    return fail(h, XFLAT_ERR_UNSUPPORTED, "the adjoint is built for one two-flavour bulb-model instance");
   HostInst& I = h->inst[0];
   if (!I.spectra) return fail(h, XFLAT_ERR_STATE, "set_spectra before the adjoint");
   if (!is_fin(r0_km) || !is_fin(r1_km) || r0_km < I.cfg.R_km || !(r1_km > r0_km))

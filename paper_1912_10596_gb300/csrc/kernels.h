@@ -6,5 +6,8 @@ struct KParams;
 // The __global__ step kernel for (n_flavor, precision, integrator) built for the requested block
 // size and resident blocks per SM (mixed two-flavour kernels: 256 x 2 or 3, or 512 x 1; all others:
 // up to 256 threads, one block), or nullptr.
-const void* step_kernel_ptr(int n_flavor, int precision, int integrator, int block, int blocks_per_sm);
+const void* step_kernel_ptr(int n_flavor, int precision, int integrator, int block, int blocks_per_sm,
+                            bool extended = false);
+// The extended bulb model's step kernels (two flavours, up to 256 threads, one block per SM).
+const void* step_kernel_ptr_2e(int precision, int integrator, int block);
 }  // namespace xflat

@@ -6,7 +6,9 @@ namespace xflat {
 
 const void* step_kernel_ptr_2f(int precision, int integrator, int block, int blocks_per_sm);
 
-const void* step_kernel_ptr(int n_flavor, int precision, int integrator, int block, int blocks_per_sm) {
+const void* step_kernel_ptr(int n_flavor, int precision, int integrator, int block, int blocks_per_sm,
+                            bool extended) {
+  if (extended) return n_flavor == 2 ? step_kernel_ptr_2e(precision, integrator, block) : nullptr;
   if (n_flavor == 2) return step_kernel_ptr_2f(precision, integrator, block, blocks_per_sm);
   if (n_flavor != 3 || block > 256) return nullptr;
   if (precision == 0) {

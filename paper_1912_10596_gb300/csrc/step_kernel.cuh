@@ -167,6 +167,7 @@ __device__ __forceinline__ void geometry_f(double u, double x, float& q, float& 
 template <typename Real>
 struct Phys2 {
   static constexpr bool kF32 = sizeof(Real) == 4;
+  static constexpr bool kPairable = kF32;       // FP32 passes run beam pairs (PairRK)
   static constexpr int NC = 3, NM = kNM2, NSC = kNSC2, KT = kF32 ? 24 : 8;
   enum : int { vT1 = 0, vQ = 1, vQBX = 2, vQBZ = 3, vG0X = 4, vG0Y = 5, vG0Z = 6,
                vNQBX = 7, vNQBZ = 8, vNG0X = 9, vNG0Y = 10, vNG0Z = 11 };
@@ -228,6 +229,20 @@ struct Phys2 {
 #pragma unroll
     for (int i = 0; i < 3; ++i) { acc[i] += wt * y[i]; acc[3 + i] += w * y[i]; }
   }
+  __device__ static inline void accum_row(Real (&acc)[NM], Real w, const Real* row, const Real (&y)[3]) {
+    accum(acc, w, t1(row), y);
+  }
+  // table row of (stage with constants sc / scf and R^2/r^2 = x, angle bin at u)
+  __device__ static inline void fill_row(Real* row, double u, double x, const double* sc, const Real* scr,
+                                         const Consts& C, int, int) {
+    if constexpr (kF32) {
+      float q, t1v, t2;
+      geometry_f(u, x, q, t1v, t2);
+      fill_f(row, q, t1v, t2, reinterpret_cast<const float*>(scr), C);
+    } else {
+      fill(row, geometry(u, x), sc, C);
+    }
+  }
   // Frobenius norm^2 of the traceless part of P = (1 + s.sigma)/2: |s|^2 / 2
   __device__ static inline Real tnorm2(const Real (&y)[3]) {
     return Real(0.5) * (y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
@@ -257,6 +272,7 @@ struct Phys2 {
 // Table row (KT = 4): q, t1, t2, pad; the stage constants mu D, mu J1, lambda stay per stage.
 template <typename Real>
 struct Phys3 {
+  static constexpr bool kPairable = false;
   static constexpr int NC = 9, NM = kNM3, NSC = kNSC3, KT = 4;
   struct Consts { double M21[6], M31[6]; };
   struct Beam { Real o21, o31; Real w; };
@@ -350,7 +366,79 @@ struct Phys3 {
     return m * sqrt(d + 2 * o);
   }
   __device__ static inline void normalise(Real (&)[9]) {}
+  __device__ static inline void accum_row(Real (&acc)[NM], Real w, const Real* row, const Real (&y)[NC]) {
+    accum(acc, w, t1(row), y);
+  }
+  __device__ static inline void fill_row(Real* row, double u, double x, const double* sc, const Real* scr,
+                                         const Consts& C, int, int) {
+    if constexpr (sizeof(Real) == 4) {
+      float q, t1v, t2;
+      geometry_f(u, x, q, t1v, t2);
+      fill_f(row, q, t1v, t2, reinterpret_cast<const float*>(scr), C);
+    } else {
+      fill(row, geometry(u, x), sc, C);
+    }
+  }
 };
+// Two flavours, extended bulb model (Sec. 2, Eq. int-v and Eq. F): beams also carry an azimuthal
+// angle phi around the radial direction, the combined angle bin a = j n_phi + p holding u_j,
+// du_j / n_phi and phi_p = 2 pi (p + 1/2) / n_phi.  Besides D and J1 the potential needs
+//   Jc = sum_b w_b (sin th_b / cos th_b) cos phi_b s_b,   Js = the same with sin phi_b,
+// and K = [eta omega B + lambda z + mu (D + (1 - cos th) J1 - sin th (cos phi Jc + sin phi Js))] / cos th.
+// Table row (KT = 10): t1, q, q Bx, q Bz, G0 (3), (sin th / cos th) cos phi, (sin th / cos th) sin phi.
+template <typename Real>
+struct Phys2E {
+  static constexpr bool kPairable = false;
+  static constexpr int NC = 3, NM = 12, NSC = 14, KT = 10;
+  enum : int { vT1 = 0, vQ = 1, vQBX = 2, vQBZ = 3, vG0X = 4, vG0Y = 5, vG0Z = 6, vSCC = 7, vSCS = 8 };
+  struct Consts { double B[3]; int n_phi; };
+  using Beam = typename Phys2<Real>::Beam;
+
+  __device__ static inline Real t1(const Real* t) { return t[vT1]; }
+  // sc: mu D (3), mu J1 (3), mu Jc (3), mu Js (3), lambda
+  __device__ static inline void fill_row(Real* t, double u, double x, const double* sc, const Real*,
+                                         const Consts& C, int a, int) {
+    const Geo g = geometry(u, x);
+    const int pidx = a % C.n_phi;
+    double sp, cp;
+    sincospi((2.0 * pidx + 1.0) / C.n_phi, &sp, &cp);         // phi_p = 2 pi (p + 1/2) / n_phi
+    const double so = sqrt(u * x) * g.q;                      // sin th / cos th, sin^2 th = u R^2 / r^2
+    t[vT1] = (Real)g.t1;
+    t[vQ] = (Real)g.q;
+    t[vQBX] = (Real)(g.q * C.B[0]);
+    t[vQBZ] = (Real)(g.q * C.B[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double ext = cp * sc[6 + i] + sp * sc[9 + i];
+      t[vG0X + i] = (Real)(g.q * ((i == 2 ? sc[12] : 0.0) + sc[i] + g.t2 * sc[3 + i]) - so * ext);
+    }
+    t[vSCC] = (Real)(so * cp);
+    t[vSCS] = (Real)(so * sp);
+    t[9] = 0;
+  }
+  __device__ static inline void K(const Real* t, const Beam& bm, const Real*, const Real*, Real (&Kv)[3]) {
+    Kv[0] = bm.eo * t[vQBX] + t[vG0X];
+    Kv[1] = t[vG0Y];
+    Kv[2] = bm.eo * t[vQBZ] + t[vG0Z];
+  }
+  __device__ static inline void f(const Real (&Kv)[3], const Real (&y)[3], Real (&k)[3]) {
+    Phys2<Real>::f(Kv, y, k);
+  }
+  __device__ static inline void accum_row(Real (&acc)[NM], Real w, const Real* t, const Real (&y)[3]) {
+    const Real wt = w * t[vT1], wc = w * t[vSCC], ws = w * t[vSCS];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      acc[i] += wt * y[i];
+      acc[3 + i] += w * y[i];
+      acc[6 + i] += wc * y[i];
+      acc[9 + i] += ws * y[i];
+    }
+  }
+  __device__ static inline Real tnorm2(const Real (&y)[3]) { return Phys2<Real>::tnorm2(y); }
+  __device__ static inline Real enorm(const Real (&e)[3]) { return Phys2<Real>::enorm(e); }
+  __device__ static inline void normalise(Real (&y)[3]) { Phys2<Real>::normalise(y); }
+};
+
 
 // --------------------------------------------------------------------------------------------
 struct KParams {
@@ -823,7 +911,7 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
       Phys::f(Kv, Y, k[l]);
     }
     if (kKind == kInitPass) {
-      Phys::accum(acc, bm.w, Phys::t1(tv.row(1, tj)), y);
+      Phys::accum_row(acc, bm.w, tv.row(1, tj), y);
       return;
     }
     if (kKind == kStagePass) {
@@ -851,13 +939,13 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
           ep[i] = v;
         }
         ep[NC] = bs.atol + bs.rtol * sqrt(fmax(Phys::tnorm2(y), Phys::tnorm2(Y)));
-        Phys::accum(acc, bm.w, Phys::t1(tv.row(I, tj)), Y);
+        Phys::accum_row(acc, bm.w, tv.row(I, tj), Y);
 #pragma unroll
         for (int i = 0; i < NC; ++i) y[i] = Y[i];
         return;
       }
       if (Tab::kAdaptive && I == Tab::S && mixed) Phys::normalise(Y);
-      Phys::accum(acc, bm.w, Phys::t1(tv.row(I, tj)), Y);
+      Phys::accum_row(acc, bm.w, tv.row(I, tj), Y);
       return;
     }
     if (Tab::kAdaptive && !kSplit) {
@@ -927,7 +1015,7 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
     }
     const bool ynok = Phys::tnorm2(yn) <= rbig<Real>();
     if (mixed && ynok) Phys::normalise(yn);
-    Phys::accum(acc, bm.w, Phys::t1(tv.row(Tab::S, tj)), yn);
+    Phys::accum_row(acc, bm.w, tv.row(Tab::S, tj), yn);
 #pragma unroll
     for (int i = 0; i < NC; ++i) y[i] = yn[i];
   }
@@ -943,7 +1031,7 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
                                      Real (&)[NC + 1],
                                      Real (&acc)[Phys::NM], Real& emax, int& bad, bool mixed) {
     if (kKind == kInitPass) {
-      Phys::accum(acc, bm.w, Phys::t1(tv.row(1, tj)), y);
+      Phys::accum_row(acc, bm.w, tv.row(1, tj), y);
       return;
     }
     const Real h = bs.hB[0];
@@ -956,7 +1044,7 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
 #pragma unroll
         for (int i = 0; i < 3; ++i) Om[i] = Real(0.5) * h * K1[i];
         rotate(Om, y);
-        Phys::accum(acc, bm.w, Phys::t1(tv.row(2, tj)), y);
+        Phys::accum_row(acc, bm.w, tv.row(2, tj), y);
         return;
       }
       Real K2[3], yn[3], ye[3], e[3];
@@ -976,7 +1064,7 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
       if (!(r2 <= rbig<Real>()) || !ynok) r2 = Real(INFINITY);
       emax = fmax(emax, r2);
       if (mixed && ynok) Phys::normalise(yn);
-      Phys::accum(acc, bm.w, Phys::t1(tv.row(3, tj)), yn);
+      Phys::accum_row(acc, bm.w, tv.row(3, tj), yn);
 #pragma unroll
       for (int i = 0; i < 3; ++i) y[i] = yn[i];
       return;
@@ -987,7 +1075,7 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
 #pragma unroll
       for (int i = 0; i < 3; ++i) Om[i] = Real(0.5) * h * K1[i];
       rotate(Om, y);
-      Phys::accum(acc, bm.w, Phys::t1(tv.row(2, tj)), y);
+      Phys::accum_row(acc, bm.w, tv.row(2, tj), y);
       return;
     }
     Phys::K(tv.row(2, tj), bm, bs.vac, bs.scr[2], K2);
@@ -995,7 +1083,7 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
 #pragma unroll
       for (int i = 0; i < 3; ++i) Om[i] = Real(0.5) * h * K2[i];
       rotate(Om, y);
-      Phys::accum(acc, bm.w, Phys::t1(tv.row(3, tj)), y);
+      Phys::accum_row(acc, bm.w, tv.row(3, tj), y);
       return;
     }
     Phys::K(tv.row(3, tj), bm, bs.vac, bs.scr[3], K3);
@@ -1006,7 +1094,7 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
 #pragma unroll
       for (int i = 0; i < 3; ++i) Om[i] = h * K3[i] - Real(0.5) * h * K1[i];
       rotate(Om, y);
-      Phys::accum(acc, bm.w, Phys::t1(tv.row(4, tj)), y);
+      Phys::accum_row(acc, bm.w, tv.row(4, tj), y);
       return;
     }
     Phys::K(tv.row(4, tj), bm, bs.vac, bs.scr[4], K4);
@@ -1019,7 +1107,7 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
       Om[i] = h * (Real(-1.0 / 12.0) * K1[i] + Real(1.0 / 6.0) * (K2[i] + K3[i]) + Real(0.25) * K4[i]);
     rotate(Om, y);
     if (mixed) Phys::normalise(y);
-    Phys::accum(acc, bm.w, Phys::t1(tv.row(4, tj)), y);
+    Phys::accum_row(acc, bm.w, tv.row(4, tj), y);
   }
 };
 
@@ -1385,6 +1473,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     typename Phys::Consts C;
     if constexpr (Phys::NC == 3) {
       C.B[0] = ic.B[0]; C.B[1] = ic.B[1]; C.B[2] = ic.B[2];
+      if constexpr (Phys::NM == 12) C.n_phi = (int)ic.n_phi;
     } else {
 #pragma unroll
       for (int i = 0; i < 6; ++i) { C.M21[i] = ic.M21[i]; C.M31[i] = ic.M31[i]; }
@@ -1395,13 +1484,9 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       const int s = t / n_jj, tj = t % n_jj;
       if (!((fill >> s) & 1u)) continue;
       Real* row = tab + ((size_t)s * n_jj + tj) * Phys::KT;
-      if constexpr (sizeof(Real) == 4) {
-        float q, t1, t2;
-        geometry_f(ut[tj], bs.xs[s], q, t1, t2);
-        Phys::fill_f(row, q, t1, t2, bs.scr[s], C);
-      } else {
-        Phys::fill(row, geometry(ut[tj], bs.xs[s]), bs.scd[s], C);
-      }
+      const int jj = (int)pc.jj_lo + tj;
+      const int a = jj >= (int)ic.n_angle ? jj - (int)ic.n_angle : jj;     // angle bin of its species
+      Phys::fill_row(row, ut[tj], bs.xs[s], bs.scd[s], bs.scr[s], C, a, 0);
     }
     __syncthreads();
     const TabView<Real, Phys> tv{tab, n_jj};
@@ -1421,7 +1506,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     Real emax = 0;
     int bad = 0;
     // FP32 two-flavour RK passes run beam pairs on packed f32x2 arithmetic (PairRK)
-    constexpr bool kPair = sizeof(Real) == 4 && NC == 3 && !kCF;
+    constexpr bool kPair = Phys::kPairable && !kCF;
     F2 acc2[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
     float emax2 = 0.0f;
     const uint32_t end = pc.start + pc.len;

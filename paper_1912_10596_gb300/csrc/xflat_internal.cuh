@@ -36,7 +36,7 @@ struct InstConst {
   uint32_t n_beams;         // 2 * n_angle * n_energy
   uint32_t n_energy, n_angle;
   uint32_t e_off, a_off;    // offsets into the energy and angle tables
-  uint32_t pad0;
+  uint32_t n_phi;           // azimuthal bins of the extended bulb model (n_angle counts u x phi)
   uint64_t div_magic;       // floor(2^40 / n_energy) + 1: q = (l * magic) >> 40 is l / n_energy
   double R2;                // R^2 (km^2)
   double mu_coef;           // mu(r) = mu_coef / r^2, includes the weight scale wscale

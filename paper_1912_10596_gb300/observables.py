@@ -25,17 +25,23 @@ def snapshot(solver: "xflat.Solver", inst: int = 0, u_bins=None) -> dict:
     spectra were set with (None: the default equal bins at midpoints)."""
     cfg = solver.cfgs[inst]
     na, ne = cfg.n_angle, cfg.n_energy
+    nphi = cfg.n_phi if cfg.n_phi >= 2 else 1
     u = (np.arange(na) + 0.5) / na if u_bins is None else np.asarray(u_bins, dtype=np.float64)
     pee, mean = solver.pee(inst=inst)
-    return {
+    shape = (na, ne) if nphi == 1 else (na, nphi, ne)      # extended bulb model: azimuthal bins too
+    half = na * nphi * ne
+    snap = {
         "r_km": np.float64(solver.stats(inst).r_km),
         "E_MeV": energy_bins(cfg),
         "theta_R_rad": np.arcsin(np.sqrt(u)),
-        "pee_nu": pee[: na * ne].reshape(na, ne),
-        "pee_nubar": pee[na * ne:].reshape(na, ne),
+        "pee_nu": pee[:half].reshape(shape),
+        "pee_nubar": pee[half:].reshape(shape),
         "pee_mean_nu": np.float64(mean),
         "flux": solver.flux_spectra(inst),           # [species, flavour, energy]
     }
+    if nphi > 1:
+        snap["phi_rad"] = 2.0 * np.pi * (np.arange(nphi) + 0.5) / nphi
+    return snap
 
 
 def save(path: str, snap: dict) -> None:

@@ -30,7 +30,7 @@ class xflat_config(C.Structure):
     _fields_ = [
         ("abi_version", C.c_uint32), ("n_flavor", C.c_uint32), ("n_energy", C.c_uint32),
         ("n_angle", C.c_uint32), ("precision", C.c_uint32), ("integrator", C.c_uint32),
-        ("matter_kind", C.c_uint32), ("reserved0", C.c_uint32),
+        ("matter_kind", C.c_uint32), ("n_phi", C.c_uint32),
         ("R_km", C.c_double), ("E_min_MeV", C.c_double), ("E_max_MeV", C.c_double),
         ("dm2_eV2", C.c_double * 2), ("theta", C.c_double * 3),
         ("rtol", C.c_double), ("atol", C.c_double), ("h0_km", C.c_double),
@@ -70,6 +70,7 @@ _SIGS = {
     "xflat_advance_graph": (_H, C.c_uint32, C.c_uint32, C.POINTER(C.c_int)),
     "xflat_moments": (_H, _P, _P),
     "xflat_moments_inst": (_H, C.c_uint32, _P, _P),
+    "xflat_moments_phi": (_H, C.c_uint32, _P, _P),
     "xflat_get_rho": (_H, _P, C.c_int, C.c_int),
     "xflat_get_rho_inst": (_H, C.c_uint32, _P, C.c_int, C.c_int),
     "xflat_set_rho": (_H, _P, C.c_int, C.c_int, C.c_double),
@@ -175,7 +176,7 @@ class Solver:
 
     def nbeams(self, inst=0):
         c = self.cfgs[inst]
-        return 2 * c.n_energy * c.n_angle
+        return 2 * c.n_energy * c.n_angle * (c.n_phi if c.n_phi >= 2 else 1)
 
     def set_spectra(self, N, u=None, du=None, inst=0):
         N = np.ascontiguousarray(N, dtype=np.float64)
@@ -210,6 +211,13 @@ class Solver:
         J1 = np.zeros(2 * n * n)
         _check(_lib.xflat_moments_inst(self.h, inst, _ptr(J0), _ptr(J1)), self.h)
         return (J0[0::2] + 1j * J0[1::2]).reshape(n, n), (J1[0::2] + 1j * J1[1::2]).reshape(n, n)
+
+    def moments_phi(self, inst=0):
+        """Azimuthal moments (Jc, Js) of the extended bulb model, 2x2 complex."""
+        Jc = np.zeros(8)
+        Js = np.zeros(8)
+        _check(_lib.xflat_moments_phi(self.h, inst, _ptr(Jc), _ptr(Js)), self.h)
+        return (Jc[0::2] + 1j * Jc[1::2]).reshape(2, 2), (Js[0::2] + 1j * Js[1::2]).reshape(2, 2)
 
     def get_rho(self, layout=LAYOUT_MATRIX, inst=0, device_ptr=None):
         """Host copy (numpy) of the state, or a copy into device memory at device_ptr."""
