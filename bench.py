@@ -170,17 +170,18 @@ def e2e_steps(xf, torch, s, wl, steps):
     r = s.stats().r_km
     import ctypes
     torch.cuda.synchronize()
+    st_a = s.stats()
     t0 = time.perf_counter()
-    bsu = 0
     for _ in range(steps):
-        st_a = s.stats()
         xf.xflat_set_rho(s.h, ctypes.c_void_p(host_state.data_ptr()), 0, xf.LAYOUT_NATIVE, r)
         s.advance([wl.r1], max_steps=1)
         xf.xflat_pee(s.h, ctypes.c_void_p(pee_host.data_ptr()), None)
-        st_b = s.stats()
-        bsu += (st_b.beam_stage_updates - st_a.beam_stage_updates)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    st_b = s.stats()
+    # every call of the loop restarts from the same state at the same radius: count its stages
+    # (the stats accumulate over the calls; a set_rho is not a stage)
+    bsu = st_b.beam_stage_updates - st_a.beam_stage_updates
     return bsu / dt, host_state.numel() * 8, pee_host.numel() * 8
 
 

@@ -255,25 +255,31 @@ __global__ void k_pee(const Real* src, uint64_t stride, uint32_t n, int nf, doub
   pee[b] = nf == 2 ? 0.5 * (1.0 + (double)src[2 * stride + b]) : (double)src[b];
 }
 
-__global__ void k_pee_mean(const double* pee, const double* N_e, const double* du, uint32_t ne, uint32_t na,
-                           double* out) {
-  __shared__ double sn[1024], sd[1024];
-  double num = 0, den = 0;
-  const uint32_t nnu = ne * na;
-  for (uint32_t b = threadIdx.x; b < nnu; b += blockDim.x) {
-    const uint32_t j = b / ne, k = b % ne;
-    const double w = du[j] * N_e[k];
-    num += w * pee[b];
-    den += w;
-  }
+// Number-flux weighted mean of P_ee over nu beams, deterministic and spread over the GPU (the
+// sums are FP64, whose pipe is narrow: one block would take milliseconds at 2M beams).  One warp
+// per angle bin sums N_e,k P_ee over energies (lanes in a fixed order, then a fixed shuffle tree);
+// one block then sums du_j times the rows in a fixed tree.
+__global__ void k_pee_rows(const double* pee, const double* N_e, uint32_t ne, uint32_t na, double* rows) {
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= na) return;
+  double s = 0.0;
+  for (uint32_t k = lane; k < ne; k += 32) s += N_e[k] * pee[(uint64_t)warp * ne + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) rows[warp] = s;
+}
+
+__global__ void k_pee_final(const double* rows, const double* du, uint32_t na, double den, double* out) {
+  __shared__ double sn[1024];
+  double num = 0.0;
+  for (uint32_t j = threadIdx.x; j < na; j += blockDim.x) num += du[j] * rows[j];
   sn[threadIdx.x] = num;
-  sd[threadIdx.x] = den;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) { sn[threadIdx.x] += sn[threadIdx.x + s]; sd[threadIdx.x] += sd[threadIdx.x + s]; }
+    if ((int)threadIdx.x < s) sn[threadIdx.x] += sn[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[0] = sd[0] > 0 ? sn[0] / sd[0] : 0.0;
+  if (threadIdx.x == 0) out[0] = den > 0 ? sn[0] / den : 0.0;
 }
 
 // Number-flux energy spectra: one thread per (species, flavour a, energy k), angle bins summed in
@@ -1095,17 +1101,23 @@ int xflat_pee_inst(xflat_t h, uint32_t inst, double* pee_per_beam, double* pee_m
   if ((rc = download_dyn(h))) return rc;
   const HostInst& I = h->inst[inst];
   const uint32_t n = I.n_beams, ne = I.cfg.n_energy, na = angle_bins(I.cfg);
-  const size_t need = ((size_t)n + ne + 2) * 8;
+  const size_t need = ((size_t)n + ne + na + 2) * 8;
   if ((rc = ensure_stage(h, need))) return rc;
   double* pee = h->d_stage;
   double* Ne = pee + n;
-  double* mean = Ne + ne;
+  double* rows = Ne + ne;
+  double* mean = rows + na;
   const void* src = cur_plane(h, inst);
   const unsigned nb = (n + 255) / 256;
   if (h->real_size == 8) k_pee<double><<<nb, 256, 0, h->stream>>>((const double*)src, h->stride, n, h->nf, pee);
   else k_pee<float><<<nb, 256, 0, h->stream>>>((const float*)src, h->stride, n, h->nf, pee);
   CUDA_TRY(h, cudaMemcpyAsync(Ne, I.N.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, h->stream));
-  k_pee_mean<<<1, 1024, 0, h->stream>>>(pee, Ne, h->d_du + I.a_off, ne, na, mean);
+  // denominator sum_j du_j sum_k N_e,k (host, fixed order)
+  double sN = 0.0, sdu = 0.0;
+  for (uint32_t k = 0; k < ne; ++k) sN += I.N[k];
+  for (uint32_t j = 0; j < na; ++j) sdu += I.du[j];
+  k_pee_rows<<<(unsigned)((32ull * na + 255) / 256), 256, 0, h->stream>>>(pee, Ne, ne, na, rows);
+  k_pee_final<<<1, 1024, 0, h->stream>>>(rows, h->d_du + I.a_off, na, sN * sdu, mean);
   CUDA_TRY(h, cudaGetLastError());
   if (pee_per_beam) CUDA_TRY(h, cudaMemcpyAsync(pee_per_beam, pee, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
   if (pee_mean) CUDA_TRY(h, cudaMemcpyAsync(pee_mean, mean, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
