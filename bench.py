@@ -289,7 +289,8 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * sum(per_step) / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": wl.name + " (oracle sample: 1000 E x 20 u x 2 = 40000 beams)"},
+                "config": {"workload": wl.name, "beams": wl.n_beams, "integrator": "dp45",
+                           "r_start_km": 11.0, "sample_beams": 2 * 20 * wl.n_energy},
                 "cpu_baseline": {"value": value, "unit": "beam-updates/s", "cores": 1, "kind": "oracle",
                                  "sample": "FP64 numpy oracle, Dormand-Prince steps at r = 11 km on 1000 E x first 20 of 2000 u bins x (nu, nubar)"},
                 "e2e": {"value": value, "unit": "beam-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
