@@ -34,8 +34,8 @@ L2_BYTES = 129 * 1024 * 1024
 # dram__bytes_write.sum of one ncu capture of an 8-step launch after the L2 flush,
 # profiles/step_kernel_mixed_dp45_4M.md).  It holds only for that launch size and for the kernel
 # sources it was taken on, identified by their SHA-256; otherwise the benchmark reports null.
-STEP_TRAFFIC = {"bytes_per_launch": 51098368 + 181353984, "steps_per_launch": 8,
-                "sources_sha256": "d1f5a4018a5b2cb7cb2a502943f8900ae2b6b8b5b9c2e3773d5d3553f9fe4f5e"}
+STEP_TRAFFIC = {"bytes_per_launch": 50919424 + 180605440, "steps_per_launch": 8,
+                "sources_sha256": "f8bc65e57c01c36f9bfb8e36101dbb38a0d648063ccf08c812997ee37e7491e8"}
 KERNEL_SOURCES = ["step_kernel.cuh", "xflat_internal.cuh", "kernels_2f.cu"]
 
 
@@ -252,6 +252,125 @@ def compare_integrators():
                           "workload": wl.name, "window_km": [r0, r1]}))
 
 
+def measure_configs():
+    """Device rates of the other workloads (they are parity-test configurations, not benchmark
+    lines): CUDA events on the launching stream, the L2 flushed before every timed launch.  One
+    JSON line per workload: beam-stage updates per second, time per step, and the algorithmic
+    bytes per beam-stage over the launch time against the measured HBM copy bandwidth.
+
+    * 4096-beam case (64 E x 32 u, FP64): commutator RK4 with its step (0.0945 km) over 100 -> 200 km,
+      and Lie RK4 (CF4) over the whole 11 -> 200 km in 2000 steps;
+    * three flavours (256 E x 512 u, FP64 DP45, both hierarchies): a window of steps from 11 km;
+    * 64 batched instances (mixed DP45, about 29 M beams): a window of steps from 11 km, one
+      persistent launch per chunk for all instances;
+    * adjoint (200 E x 400 u, FP64 RK4, 5000 steps over 100 -> 300 km, checkpoints every 64 steps):
+      time per gradient."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_10596_gb300 import xflat as xf
+    from bulb_inputs import workload_2f_small_fp64, workload_3f_fp64, batched_workloads, workload_adjoint
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    hbm, peak_kind = _peaks()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def line(name, beams, bsu, ms, steps, bpbs, **extra):
+        rate = bsu / (ms / 1e3)
+        out = {"workload": name, "beams": beams, "beam_stage_updates": bsu, "device_ms": ms,
+               "ms_per_step": ms / steps if steps else None, "beam_updates_per_s": rate,
+               "bytes_per_beam_stage": bpbs,
+               "hbm_frac": (bpbs * rate / 1e9) / hbm if bpbs else None, "peak": f"{hbm} GB/s ({peak_kind})"}
+        out.update(extra)
+        print(json.dumps(out), flush=True)
+
+    def solver(cfgs, spectra):
+        for c in cfgs:
+            c.cuda_stream = stream.cuda_stream
+        sv = xf.Solver(cfgs)
+        for i, N in enumerate(spectra):
+            sv.set_spectra(N, inst=i)
+        return sv
+
+    def window(sv, r1s, steps, per_launch=8, warmup=3):
+        """Time `steps` steps of every instance from its current radius (launches of per_launch
+        steps, L2 flushed before each); returns (ms, beam-stage updates)."""
+        sv.advance(r1s, max_steps=1)
+        for _ in range(warmup - 1):
+            sv.advance(None, max_steps=1)
+        torch.cuda.synchronize()
+        b0 = sv.stats(0).beam_stage_updates                  # the handle's total over its instances
+        ms = 0.0
+        for n in launch_chunks(steps, per_launch):
+            flush_l2(flush_buf)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            sv.advance(None, max_steps=n)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        st = [sv.stats(i) for i in range(sv.n_inst)]
+        if any(x.status != 0 for x in st):
+            raise RuntimeError("device status " + str([x.status for x in st]))
+        return ms, st[0].beam_stage_updates - b0
+
+    # 4096-beam case: whole radial ranges, one xflat_evolve each (warm-up run first)
+    wl = workload_2f_small_fp64()
+    h = (wl.r1 - wl.r0) / wl.n_steps
+    for integ, r0 in (("rk4", 100.0), ("lie_rk4", wl.r0)):
+        sv = solver([xf.config_from_workload(wl, integrator=integ, fixed_dr_km=h)], [wl.spectra()])
+        for rep in range(2):
+            sv.reset(r0)
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            sv.evolve(r0, wl.r1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        st = sv.stats()
+        steps = int(st.accepted)
+        line(f"{wl.name} ({integ}, {r0:g} -> {wl.r1:g} km)", wl.n_beams, st.beam_stage_updates,
+             e0.elapsed_time(e1), steps, 30.0, passes_per_step=4,
+             us_per_pass=1e3 * e0.elapsed_time(e1) / (4 * steps))
+        sv.close()
+
+    # three flavours, both hierarchies
+    for dm31 in (2.4e-3, -2.4e-3):
+        wl = workload_3f_fp64(dm31)
+        sv = solver([xf.config_from_workload(wl)], [wl.spectra()])
+        ms, bsu = window(sv, [wl.r1], 16)
+        line(wl.name, wl.n_beams, bsu, ms, 16, 84.0, window="16 DP45 steps from 11 km")
+        sv.close()
+
+    # 64 batched instances
+    wls = batched_workloads()
+    sv = solver([xf.config_from_workload(w) for w in wls], [w.spectra() for w in wls])
+    ms, bsu = window(sv, [w.r1 for w in wls], 16)
+    total = sum(w.n_beams for w in wls)
+    line("batched 64 instances (seed 0x5EED0003)", total, bsu, ms, 16, 14.0,
+         window="16 DP45 steps of every instance from 11 km", state_bytes=12 * total)
+    sv.close()
+
+    # adjoint
+    wl = workload_adjoint()
+    r0, r1 = 100.0, 300.0
+    sv = solver([xf.config_from_workload(wl, fixed_dr_km=(r1 - r0) / wl.n_steps)], [wl.spectra()])
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sv.adjoint(r0, r1, wl.n_steps, 64)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    fwd = wl.n_beams * 4 * wl.n_steps
+    line(f"{wl.name} ({r0:g} -> {r1:g} km, K = 64)", wl.n_beams, fwd, 1e3 * dt, wl.n_steps, None,
+         seconds_per_gradient=dt, note="beam_stage_updates counts the forward stages only; the "
+         "gradient also recomputes every segment and runs the adjoint sweep (wall clock around xflat_adjoint)")
+    sv.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,9 +385,14 @@ def main():
                     help="radial steps per persistent launch in the timed region (L2 flushed before each)")
     ap.add_argument("--compare-integrators", action="store_true",
                     help="accuracy against cost of the integrators on the 4096-beam case instead of the benchmark")
+    ap.add_argument("--configs", action="store_true",
+                    help="device rates of the other workloads (small, three-flavour, batched, adjoint) instead of the benchmark")
     args = ap.parse_args()
     if args.compare_integrators:
         compare_integrators()
+        return
+    if args.configs:
+        measure_configs()
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

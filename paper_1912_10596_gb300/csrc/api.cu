@@ -54,6 +54,7 @@ struct xflat_s {
   // device memory
   void* planes = nullptr;                  // [2][nc][stride] Real
   void* escr = nullptr;                    // DP45: error partial + scale planes [nc + 1][stride] Real
+  void* kst = nullptr;                     // FP64 RK4 / DP45: stage derivatives + one stage state [n + 1][nc][stride] Real
   uint64_t stride = 0;
   InstConst* d_ic = nullptr;
   InstDyn* d_dyn = nullptr;
@@ -471,6 +472,7 @@ KParams make_params(xflat_t h, int n_steps, int init_only) {
   p.planeA = h->planes;
   p.planeB = (char*)h->planes + (size_t)h->nc * h->stride * h->real_size;
   p.escr = h->escr;
+  p.kst = h->kst;
   p.plane_stride = h->stride;
   p.etab = h->d_etab;
   p.u_tab = h->d_u;
@@ -779,6 +781,11 @@ int create_impl(const xflat_config* cfgs, uint32_t n, xflat_t* out) {
   if (h->integrator == XFLAT_DP45 && h->real_size == 8 &&
       cudaMalloc(&h->escr, (size_t)(h->nc + 1) * h->stride * h->real_size) != cudaSuccess)
     return bail(XFLAT_ERR_NOMEM);
+  // FP64 RK4 / DP45: the stage derivatives a step stores (k_1..k_3 of RK4, k_1..k_5 of DP45, whose
+  // pass forming y5 keeps the error partial instead of k_6), then one stage state
+  const int n_kst = h->real_size != 8 ? 0 : h->integrator == XFLAT_RK4 ? 3 : h->integrator == XFLAT_DP45 ? 5 : 0;
+  if (n_kst && cudaMalloc(&h->kst, (size_t)(n_kst + 1) * h->nc * h->stride * h->real_size) != cudaSuccess)
+    return bail(XFLAT_ERR_NOMEM);
   if (cudaMalloc(&h->d_ic, sizeof(InstConst) * n) != cudaSuccess ||
       cudaMalloc(&h->d_dyn, sizeof(InstDyn) * n) != cudaSuccess ||
       cudaMalloc(&h->d_acc, sizeof(unsigned long long) * n * kAccWordsPerInst) != cudaSuccess ||
@@ -854,7 +861,7 @@ int xflat_destroy(xflat_t h) {
   if (!h) return XFLAT_OK;
   if (h->stream || true) cudaStreamSynchronize(h->stream);
   drop_graph(h);
-  void* ptrs[] = {h->planes, h->escr, h->d_ic, h->d_dyn, h->d_pieces, h->d_blk, h->d_acc, h->d_errmax,
+  void* ptrs[] = {h->planes, h->escr, h->kst, h->d_ic, h->d_dyn, h->d_pieces, h->d_blk, h->d_acc, h->d_errmax,
                   h->d_nonfinite, h->d_etab, h->d_u, h->d_du, h->d_bar, h->d_words, h->d_stage,
                   h->d_trace};
   for (void* p : ptrs)

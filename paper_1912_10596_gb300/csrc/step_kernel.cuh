@@ -454,6 +454,7 @@ struct KParams {
   void* planeA;
   void* planeB;
   void* escr;                    // adaptive tableaus: error partial and scale planes [NC + 1][plane_stride]
+  void* kst;                     // FP64 RK4 / DP45: stage derivatives k_1..k_n, then one stage state [n + 1][NC][plane_stride]
   uint64_t plane_stride;         // elements between component planes
   const void* etab;              // energy tables, Real, per instance at e_off: [n_tab][n_energy]
   const double* u_tab;           // angle positions u_j, at a_off
@@ -872,6 +873,22 @@ __host__ __device__ constexpr bool split_final() {
   return Tab::kAdaptive && !Tab::kFinalMoments && !Tab::kEM2 && sizeof(Real) == 8;   // DP45 in FP64
 }
 
+// FP64 commutator tableaus (RK4, DP45) keep their stage derivatives in HBM: the pass that
+// evaluates k_s writes it, later passes of the step read it back instead of rebuilding the chain.
+// On GB300 an FP64 stage evaluation costs far more time than moving its 8 bytes per component
+// (the FP64 pipe runs at ~1/68 of the FP32 rate), so a DP45 step evaluates 7 stages instead of
+// the 28 of the rebuilt chain.  FP32 kernels rebuild: their stage vectors would push the state out
+// of the L2.  The stored values are bit-identical to rebuilt ones (same inputs, same arithmetic).
+template <class Tab, typename Real>
+__host__ __device__ constexpr bool stored_stages() {
+  return !Tab::kEM2 && sizeof(Real) == 8;
+}
+// Stage derivatives a step stores (k_1 .. k_n): every stage whose derivative a later pass needs.
+template <class Tab, typename Real>
+__host__ __device__ constexpr int stored_stage_count() {
+  return split_final<Tab, Real>() ? Tab::S - 2 : Tab::S - 1;
+}
+
 template <class Phys, class Tab, typename Real, bool kCF, int kPass, int kKind>
 struct PassBody;
 
@@ -886,29 +903,55 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
   static constexpr int kChain =
       kKind == kInitPass ? 0
       : (kKind == kFinalPass ? (kSplit ? 0 : Tab::S - (Tab::kAdaptive ? 1 : 0)) : kPass + 1);
+  // stored stage derivatives (stored_stages): all of the chain but its last stage are read back,
+  // and a stage pass writes the one it evaluates when a later pass of the step reads it
+  static constexpr bool kStore = stored_stages<Tab, Real>();
+  static constexpr int kLoadK = (kStore && kChain > 0) ? kChain - 1 : 0;
+  static constexpr bool kStoreK = kStore && kKind == kStagePass && kChain <= stored_stage_count<Tab, Real>();
+  // the stage state the chain evaluates last, Y_kChain, is the one the previous pass formed for its
+  // moments: stored there (plane set after the stage derivatives) and read back here
+  static constexpr bool kLoadY = kStore && kChain >= 2;
+  static constexpr bool kStoreY = kStore && kKind == kStagePass && !(kSplit && kPass + 2 == Tab::S);
+  static constexpr int kYPlanes = stored_stage_count<Tab, Real>();
   // y: the step's state.  Split final pass: the pass forming Y_S replaces y by the new state
   // y5 = Y_S and sets ep = (error partial sum over stages 1..S-1, atol + rtol max(|y|, |y5|)); the
-  // final pass gets y5 in y and that ep back.
+  // final pass gets y5 in y and that ep back.  kst: this beam's element of the stage-derivative
+  // planes (component i of k_l at kst[((l - 1) NC + i) kstride]), read and written by this thread
+  // only.
   template <class BS>
   __device__ static inline void beam(const BS& bs, const typename Phys::Beam& bm,
                                      const TabView<Real, Phys>& tv, int tj, Real (&y)[NC],
                                      Real (&ep)[NC + 1],
-                                     Real (&acc)[Phys::NM], Real& emax, int& bad, bool mixed) {
+                                     Real (&acc)[Phys::NM], Real& emax, int& bad, bool mixed,
+                                     Real* kst, size_t kstride) {
     Real k[Tab::S + 1][NC];
 #pragma unroll
-    for (int l = 1; l <= kChain; ++l) {
+    for (int l = 1; l <= kLoadK; ++l)
+#pragma unroll
+      for (int i = 0; i < NC; ++i) k[l][i] = kst[((size_t)(l - 1) * NC + i) * kstride];
+#pragma unroll
+    for (int l = kLoadK + 1; l <= kChain; ++l) {
       Real Y[NC];
+      if constexpr (kLoadY) {
 #pragma unroll
-      for (int i = 0; i < NC; ++i) {
-        Real v = y[i];
+        for (int i = 0; i < NC; ++i) Y[i] = kst[((size_t)kYPlanes * NC + i) * kstride];
+      } else {
 #pragma unroll
-        for (int m = 1; m < l; ++m)
-          if (Tab::a(l, m) != 0.0) v += bs.hA[l][m] * k[m][i];
-        Y[i] = v;
+        for (int i = 0; i < NC; ++i) {
+          Real v = y[i];
+#pragma unroll
+          for (int m = 1; m < l; ++m)
+            if (Tab::a(l, m) != 0.0) v += bs.hA[l][m] * k[m][i];
+          Y[i] = v;
+        }
       }
       Real Kv[NC];
       Phys::K(tv.row(l, tj), bm, bs.vac, bs.scr[l], Kv);
       Phys::f(Kv, Y, k[l]);
+    }
+    if constexpr (kStoreK) {
+#pragma unroll
+      for (int i = 0; i < NC; ++i) kst[((size_t)(kChain - 1) * NC + i) * kstride] = k[kChain][i];
     }
     if (kKind == kInitPass) {
       Phys::accum_row(acc, bm.w, tv.row(1, tj), y);
@@ -945,6 +988,10 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
         return;
       }
       if (Tab::kAdaptive && I == Tab::S && mixed) Phys::normalise(Y);
+      if constexpr (kStoreY) {
+#pragma unroll
+        for (int i = 0; i < NC; ++i) kst[((size_t)kYPlanes * NC + i) * kstride] = Y[i];
+      }
       Phys::accum_row(acc, bm.w, tv.row(I, tj), Y);
       return;
     }
@@ -1025,11 +1072,13 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
 template <class Phys, class Tab, typename Real, int kPass, int kKind>
 struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
   static constexpr int NC = 3;
+  static constexpr bool kStore = false;
   template <class BS>
   __device__ static inline void beam(const BS& bs, const typename Phys::Beam& bm,
                                      const TabView<Real, Phys>& tv, int tj, Real (&y)[NC],
                                      Real (&)[NC + 1],
-                                     Real (&acc)[Phys::NM], Real& emax, int& bad, bool mixed) {
+                                     Real (&acc)[Phys::NM], Real& emax, int& bad, bool mixed,
+                                     Real*, size_t) {
     if (kKind == kInitPass) {
       Phys::accum_row(acc, bm.w, tv.row(1, tj), y);
       return;
@@ -1498,6 +1547,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     constexpr bool kSplitStore = split_final<Tab, Real>() && kKind == kStagePass && kPass + 2 == Tab::S;
     constexpr bool kSplitLoad = split_final<Tab, Real>() && kKind == kFinalPass;
     Real* escr = reinterpret_cast<Real*>(p.escr) + ic.beam_off;
+    Real* kst = Body::kStore ? reinterpret_cast<Real*>(p.kst) + ic.beam_off : nullptr;
     const Real* ysrc = kSplitLoad ? yout : yin;
     const int ne = (int)ic.n_energy, na = (int)ic.n_angle;
     Real acc[NM];
@@ -1584,7 +1634,8 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
 #pragma unroll
               for (int c = 0; c <= NC; ++c) ev[c] = ep[c][v];
             }
-            Body::beam(bs, bm, tv, tj, y, ev, acc, emax, bad, mixed);
+            Body::beam(bs, bm, tv, tj, y, ev, acc, emax, bad, mixed, Body::kStore ? kst + l0 + v : nullptr,
+                       p.plane_stride);
 #pragma unroll
             for (int c = 0; c < NC; ++c) ys[c][v] = y[c];
             if constexpr (kSplitStore) {
