@@ -26,7 +26,11 @@
 namespace xflat {
 namespace {
 
+constexpr int kAdjGeoSets = 5;       // radii per pass whose geometry is tabulated
+constexpr int kAdjGeoRows = 64;      // angle rows per block the table holds
+
 struct AdjShared {
+  Geo geo[kAdjGeoSets][kAdjGeoRows];    // per pass: geometry of this block's angle rows
   double scratch[32 * 6];
   double tot[8];
   double scf[kAdjStageVals];            // constants of the stage finished in this pass
@@ -38,6 +42,7 @@ struct AdjShared {
 
 struct BeamC {
   double eo, w, u, ow;                  // eta omega, moment weight, u_j, objective weight (nu)
+  uint32_t jj;                          // combined row sigma n_angle + j
 };
 
 __device__ __forceinline__ BeamC beam_consts(const AdjParams& p, uint32_t b) {
@@ -50,7 +55,28 @@ __device__ __forceinline__ BeamC beam_consts(const AdjParams& p, uint32_t b) {
   c.w = p.du[j] * p.g[sig * p.n_energy + k];
   c.u = p.u[j];
   c.ow = sig ? 0.0 : p.du[j] * p.objw[k];
+  c.jj = sig * p.n_angle + j;
   return c;
+}
+
+// Geometry (1/cos, 1/cos - 1, 1 - cos) of every angle row of the beams [b0, b1) at up to
+// kAdjGeoSets radii (R^2/r^2 = xof(set)): one FP64 square root and two divisions per (row,
+// radius) instead of per beam, which GB300 would run on its two-lane FP64 pipe.  Returns whether
+// the rows fit the table (same answer in every thread); if not, callers compute per beam.  The
+// caller's __syncthreads publishes the table.
+template <class XOf>
+__device__ bool fill_geo(const AdjParams& p, AdjShared& S, uint32_t b0, uint32_t b1, XOf xof, uint32_t& row0) {
+  row0 = b0 / p.n_energy;
+  const uint32_t last = b1 > b0 ? (b1 - 1) / p.n_energy : row0;
+  const int rows = (int)(last - row0 + 1);
+  if (b1 <= b0 || rows > kAdjGeoRows) return false;
+  for (int t = threadIdx.x; t < kAdjGeoSets * rows; t += blockDim.x) {
+    const int set = t / rows, r = t - set * rows;
+    const uint32_t jj = row0 + r;
+    const uint32_t j = jj >= p.n_angle ? jj - p.n_angle : jj;
+    S.geo[set][r] = geometry(p.u[j], xof(set));
+  }
+  return true;
 }
 
 __device__ __forceinline__ void ld3(const double* base, uint64_t n, uint32_t b, double (&x)[3]) {
@@ -129,11 +155,15 @@ __device__ bool forward_steps(const AdjParams& p, AdjShared& S, int n_first, int
     const int sp = pp > 0 ? ((pp - 1) & 3) + 1 : 0;        // stage finished in this pass
     const int s = (pp & 3) + 1, m = pp >> 2;                // stage formed in this pass
     const int nstep = n_first + m;
-    if (pp > 0) {
-      if (threadIdx.x < kAdjStageVals) S.scf[threadIdx.x] = __ldcg(&p.glob[threadIdx.x]);
-      __syncthreads();
-    }
+    if (pp > 0 && threadIdx.x < kAdjStageVals) S.scf[threadIdx.x] = __ldcg(&p.glob[threadIdx.x]);
     const double x_s = pp < P ? p.ic.R2 / (stage_radius(p, nstep, s) * stage_radius(p, nstep, s)) : 0.0;
+    // geometry sets: 0 the finished stage (its R^2/r^2 was published with its constants), 1 the
+    // formed stage
+    uint32_t row0;
+    const bool tab = fill_geo(p, S, b0, b1, [&](int set) {
+      return set == 0 ? (pp > 0 ? __ldcg(&p.glob[7]) : 0.0) : set == 1 ? x_s : 0.0;
+    }, row0);
+    __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (uint32_t b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
       const BeamC c = beam_consts(p, b);
@@ -144,7 +174,7 @@ __device__ bool forward_steps(const AdjParams& p, AdjShared& S, int n_first, int
         double ys[3], K[3], k[3], ks[3];
         const double as = sp == 1 ? 0.0 : rk_a(sp) * p.h;
         for (int i = 0; i < 3; ++i) ys[i] = sp == 1 ? y[i] : y[i] + as * kl[i];
-        const Geo g = geometry(c.u, S.scf[7]);
+        const Geo g = tab ? S.geo[0][c.jj - row0] : geometry(c.u, S.scf[7]);
         kvec(S.scf, g, c.eo, p.ic.B, K);
         cross(K, ys, k);
         if (sp == 1) {
@@ -170,7 +200,7 @@ __device__ bool forward_steps(const AdjParams& p, AdjShared& S, int n_first, int
         double ys[3];
         const double as = s == 1 ? 0.0 : rk_a(s) * p.h;
         for (int i = 0; i < 3; ++i) ys[i] = s == 1 ? y[i] : y[i] + as * kl[i];
-        const Geo g = geometry(c.u, x_s);
+        const Geo g = tab ? S.geo[1][c.jj - row0] : geometry(c.u, x_s);
         const double wt = c.w * g.t1;
         for (int i = 0; i < 3; ++i) {
           acc[i] += wt * ys[i];
@@ -246,6 +276,12 @@ __device__ bool backward_steps(const AdjParams& p, AdjShared& S) {
         S.scf[threadIdx.x] = __ldcg(&p.stage_sc[((size_t)mp * 4 + (sp - 1)) * kAdjStageVals + threadIdx.x]);
       if (threadIdx.x < 6) S.gl[threadIdx.x] = __ldcg(&p.glob[kGlobAdj + threadIdx.x]);
     }
+    // geometry sets: 0 the finished stage, 1..4 the stages of the formed stage's step
+    uint32_t row0;
+    const bool tab = fill_geo(p, S, b0, b1, [&](int set) {
+      if (set == 0) return pp > 0 ? __ldcg(&p.stage_sc[((size_t)mp * 4 + (sp - 1)) * kAdjStageVals + 7]) : 0.0;
+      return pp < P ? __ldcg(&p.stage_sc[((size_t)m * 4 + (set - 1)) * kAdjStageVals + 7]) : 0.0;
+    }, row0);
     __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (uint32_t b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
@@ -258,7 +294,7 @@ __device__ bool backward_steps(const AdjParams& p, AdjShared& S) {
         if (sp == 1) ld3(p.seg + (size_t)mp * 3 * n, n, b, ys);
         else ld3(p.ystage + (size_t)(sp - 2) * 3 * n, n, b, ys);
         ld3(p.v, n, b, v);
-        const Geo g = geometry(c.u, S.scf[7]);
+        const Geo g = tab ? S.geo[0][c.jj - row0] : geometry(c.u, S.scf[7]);
         kvec(S.scf, g, c.eo, p.ic.B, K);
         double br[3];
         for (int i = 0; i < 3; ++i) br[i] = g.t1 * S.gl[i] + S.gl[3 + i];
@@ -292,7 +328,7 @@ __device__ bool backward_steps(const AdjParams& p, AdjShared& S) {
           ld3(p.seg + (size_t)m * 3 * n, n, b, y);
           for (int i = 0; i < 3; ++i) yy[i] = y[i];
           for (int st = 1; st <= 3; ++st) {
-            const Geo g = geometry(c.u, S.scs[st - 1][7]);
+            const Geo g = tab ? S.geo[st][c.jj - row0] : geometry(c.u, S.scs[st - 1][7]);
             kvec(S.scs[st - 1], g, c.eo, p.ic.B, K);
             cross(K, yy, k);
             const double as = rk_a(st + 1) * h;
@@ -308,7 +344,7 @@ __device__ bool backward_steps(const AdjParams& p, AdjShared& S) {
         st3(p.v, n, b, v);
         double pv[3];
         cross(ys, v, pv);
-        const Geo g = geometry(c.u, S.scs[s - 1][7]);
+        const Geo g = tab ? S.geo[s][c.jj - row0] : geometry(c.u, S.scs[s - 1][7]);
         for (int i = 0; i < 3; ++i) {
           acc[i] += g.q * pv[i];
           acc[3 + i] += g.t1 * pv[i];
