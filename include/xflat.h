@@ -113,7 +113,9 @@ typedef struct {
   double lambda_const_kmi;    /* XFLAT_MATTER_CONSTANT                                             */
   void* cuda_stream;          /* cudaStream_t the handle works on (NULL = default stream)          */
   uint64_t barrier_timeout_ns;/* limit of every device-wide wait (0 = 2 s)                         */
-  uint32_t block_size;        /* threads per block: 128, 256 or 512 (0 = library default)          */
+  uint32_t block_size;        /* threads per block: 128, 256 or 512 (0 = library default: 512 for
+                                 the mixed two-flavour bulb kernels whose two state buffers fit
+                                 the L2, 256 otherwise)                                          */
   uint32_t blocks_per_sm;     /* resident blocks per SM for the persistent grid (0 = occupancy)    */
   uint32_t steps_per_launch;  /* radial steps per persistent launch in xflat_evolve (0 = 64)       */
   uint32_t reserved1;

@@ -606,8 +606,19 @@ int refresh_moments(xflat_t h) {
 int setup_launch_shape(xflat_t h, const xflat_config& c) {
   // mixed two-flavour kernels exist at two register budgets: 768 resident threads per SM (80
   // registers) and 512 (128 registers); the request picks the one that fits.  Every other kernel
-  // is built for one 256-thread block per SM.  Default: 256 threads x 3 blocks.
-  h->block = c.block_size ? (int)c.block_size : 256;
+  // is built for one 256-thread block per SM.  Default for the mixed two-flavour bulb kernels: one
+  // 512-thread block per SM while both state buffers fit the L2 (the passes are then bound by
+  // issue: the 80-register budget spills, and two co-resident blocks finish their passes at
+  // different times), three 256-thread blocks once the state streams from HBM (more loads in
+  // flight); 256 threads otherwise.  (GB300, DP45, 28M beams in 64 instances: 2.07 ms per step at
+  // 256 x 3 against 2.31 ms at 512 x 1; 4M beams in one instance: 0.186 ms per one-step launch at
+  // 512 x 1 against 0.224 ms at 256 x 3.)
+  const bool mixed_2f = h->nf == 2 && !h->extended && h->real_size == 4;
+  int l2_bytes = 0;
+  cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, h->device);
+  const uint64_t state_bytes = 2ull * h->nc * h->stride * h->real_size;
+  const bool resident = state_bytes <= (uint64_t)l2_bytes;
+  h->block = c.block_size ? (int)c.block_size : (mixed_2f && !c.blocks_per_sm && resident ? 512 : 256);
   const int want_bps = c.blocks_per_sm ? (int)c.blocks_per_sm : (768 / h->block);
   h->kernel = step_kernel_ptr(h->nf, h->precision, h->integrator, h->block, want_bps * h->block >= 768 ? 3 : 2,
                               h->extended);

@@ -141,12 +141,18 @@ def test_small_workload_full_range(xf):
     assert err < 1e-10, err
 
 
-def test_mixed_precision_against_fp64_oracle(xf):
+@pytest.mark.parametrize("shape", [(0, 0), (256, 3), (256, 2), (128, 4)])
+def test_mixed_precision_against_fp64_oracle(xf, shape):
     """FP32 per-beam algebra with FP64 moments and step control, renormalised |s|: survival
-    probabilities within 1e-4 of the FP64 oracle through a window with strong flavour evolution."""
+    probabilities within 1e-4 of the FP64 oracle through a window with strong flavour evolution,
+    for the default launch shape (one 512-thread block per SM) and the register budgets of the
+    other shapes (768 or 512 resident threads per SM)."""
     wl = Workload(name="mx", **RAGGED, integrator="dp45", rtol=1e-9, atol=1e-9, h0=1e-3)
     Y, st = oracle_run(wl, Bulb(wl).initial_state(), 100.0, 110.0)
-    s = make_solver(xf, wl, precision="mixed", rtol=1e-6, atol=1e-6)
+    s = make_solver(xf, wl, precision="mixed", rtol=1e-6, atol=1e-6, block_size=shape[0],
+                    blocks_per_sm=shape[1])
+    gs = s.stats()
+    assert gs.block_size == (shape[0] or 512)
     s.reset(100.0)
     s.evolve(100.0, 110.0)
     pee, mean = s.pee()
