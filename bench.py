@@ -252,7 +252,7 @@ def compare_integrators():
                           "workload": wl.name, "window_km": [r0, r1]}))
 
 
-def measure_configs():
+def measure_configs(only=None):
     """Device rates of the other workloads (they are parity-test configurations, not benchmark
     lines): CUDA events on the launching stream, the L2 flushed before every timed launch.  One
     JSON line per workload: beam-stage updates per second, time per step, and the algorithmic
@@ -317,10 +317,13 @@ def measure_configs():
             raise RuntimeError("device status " + str([x.status for x in st]))
         return ms, st[0].beam_stage_updates - b0
 
+    def want(name):
+        return only is None or only == name
+
     # 4096-beam case: whole radial ranges, one xflat_evolve each (warm-up run first)
     wl = workload_2f_small_fp64()
     h = (wl.r1 - wl.r0) / wl.n_steps
-    for integ, r0 in (("rk4", 100.0), ("lie_rk4", wl.r0)):
+    for integ, r0 in (("rk4", 100.0), ("lie_rk4", wl.r0)) if want("small") else ():
         sv = solver([xf.config_from_workload(wl, integrator=integ, fixed_dr_km=h)], [wl.spectra()])
         for rep in range(2):
             sv.reset(r0)
@@ -338,7 +341,7 @@ def measure_configs():
         sv.close()
 
     # three flavours, both hierarchies
-    for dm31 in (2.4e-3, -2.4e-3):
+    for dm31 in (2.4e-3, -2.4e-3) if want("3f") else ():
         wl = workload_3f_fp64(dm31)
         sv = solver([xf.config_from_workload(wl)], [wl.spectra()])
         ms, bsu = window(sv, [wl.r1], 16)
@@ -346,13 +349,17 @@ def measure_configs():
         sv.close()
 
     # 64 batched instances
-    wls = batched_workloads()
-    sv = solver([xf.config_from_workload(w) for w in wls], [w.spectra() for w in wls])
-    ms, bsu = window(sv, [w.r1 for w in wls], 16)
-    total = sum(w.n_beams for w in wls)
-    line("batched 64 instances (seed 0x5EED0003)", total, bsu, ms, 16, 14.0,
-         window="16 DP45 steps of every instance from 11 km", state_bytes=12 * total)
-    sv.close()
+    if want("batched"):
+        wls = batched_workloads()
+        sv = solver([xf.config_from_workload(w) for w in wls], [w.spectra() for w in wls])
+        ms, bsu = window(sv, [w.r1 for w in wls], 16)
+        total = sum(w.n_beams for w in wls)
+        line("batched 64 instances (seed 0x5EED0003)", total, bsu, ms, 16, 14.0,
+             window="16 DP45 steps of every instance from 11 km", state_bytes=12 * total,
+             block_size=sv.stats().block_size, blocks=sv.stats().grid_blocks)
+        sv.close()
+    if not want("adjoint"):
+        return
 
     # adjoint
     wl = workload_adjoint()
@@ -387,12 +394,14 @@ def main():
                     help="accuracy against cost of the integrators on the 4096-beam case instead of the benchmark")
     ap.add_argument("--configs", action="store_true",
                     help="device rates of the other workloads (small, three-flavour, batched, adjoint) instead of the benchmark")
+    ap.add_argument("--only", choices=["small", "3f", "batched", "adjoint"],
+                    help="with --configs: measure one of the workloads")
     args = ap.parse_args()
     if args.compare_integrators:
         compare_integrators()
         return
     if args.configs:
-        measure_configs()
+        measure_configs(args.only)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
