@@ -235,6 +235,21 @@ def test_nonfinite_state_is_reported(xf):
     assert e.value.code == xf.ERR_NONFINITE
 
 
+def test_step_underflow_is_reported(xf):
+    """DP45 from the neutrino sphere with the r^-3 matter potential (~1.5e6 /km at 11 km) and a
+    step floor far above the step that potential allows: every trial step is rejected, the step
+    shrinks below h_min and the call reports XFLAT_ERR_STEP; the handle stays usable."""
+    wl = Workload(name="uf", n_energy=8, n_angle=4, integrator="dp45", matter="power_law", h0=1e-2)
+    s = make_solver(xf, wl, h_min_km=1e-4)
+    s.reset(11.0)
+    with pytest.raises(xf.XflatError) as e:
+        s.evolve(11.0, 12.0)
+    assert e.value.code == xf.ERR_STEP
+    st = s.stats()
+    assert st.status == xf.ERR_STEP and st.accepted == 0 and st.rejected >= 3
+    assert st.r_km == 11.0
+
+
 def test_barrier_timeout_returns_status_and_context_survives(xf):
     """A barrier that waits for one arrival too many gives up after the configured limit; the call
     reports XFLAT_ERR_TIMEOUT and the next call on the same device works."""
