@@ -50,7 +50,7 @@ enum xflat_status {
   XFLAT_ERR_NONFINITE = 5,    /* a NaN or infinity appeared in the state, moments or error norm */
   XFLAT_ERR_STEP = 6,         /* adaptive step size fell below h_min_km                         */
   XFLAT_ERR_STATE = 7,        /* call order violated (e.g. evolve before set_spectra)           */
-  XFLAT_ERR_UNSUPPORTED = 8   /* valid request this build does not implement                    */
+  XFLAT_ERR_UNSUPPORTED = 8   /* valid request the library does not implement                   */
 };
 
 /* ---- configuration enums --------------------------------------------------------------------- */

@@ -12,7 +12,7 @@ orthogonal to the electron one under unitary evolution, so the sum of their proj
 (and I - Pbar); with equal mu and tau spectra (the inputs guarantee this) the flux matrix needs no
 further state.  ``oracle.four_psi`` keeps all four wavefunctions explicitly and checks this.
 
-Readings of the paper taken here (each listed in the design doc):
+Readings of the paper taken here, where it is silent or ambiguous:
 
 * Eq. Hnu integrates d(cos theta') over the directions populated at radius r, cos theta' in
   [sqrt(1 - R^2/r^2), 1]; in the equal-u bins of Sec. 3.2 (u = sin^2 theta_R) this measure is
