@@ -23,7 +23,7 @@ def gpu_available() -> bool:
 
 @pytest.fixture(scope="session")
 def xf():
-    """The C-ABI binding, loaded on a GPU machine (fails loudly if the library is missing)."""
+    """The C-ABI binding, loaded on a machine with a GPU (fails loudly if the library is missing)."""
     if not gpu_available():
         pytest.skip("no CUDA device")
     from paper_1912_10596_gb300 import xflat
