@@ -1,5 +1,6 @@
 // Throughput probe of the arithmetic and barrier figures the kernels are sized against: FP64, FP32 and
-// packed FP32x2 FMA rates, __sincosf rate, device-wide barrier latency (bounded spin), D2D copy.
+// packed FP32x2 FMA rates, __sincosf rate, device-wide barrier latency (bounded spin), the latency
+// of dependent FP64 operations, D2D copy.
 // Built and run by paper_1912_10596_gb300/probe.py (a standalone executable, not part of libxflat).
 #include <cstdio>
 #include <cstdint>
