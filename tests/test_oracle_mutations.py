@@ -1,0 +1,160 @@
+"""The oracle's pins catch plausible mistakes: each case plants one mistake in the oracle (on the
+CPU, by patching one of its functions for the duration of the case) and checks that the pins
+named beside it fail.  The mistakes are the kind a transcription of the paper's equations makes:
+a flipped sign, a dropped factor, a missing term, a wrong coefficient.
+"""
+import warnings
+
+import numpy as np
+import pytest
+
+import test_oracle_pins as pins
+from oracle import integrate as ig
+from oracle import physics as ph
+
+Bulb = ph.Bulb
+_rhs, _hff, _nff = Bulb.rhs, Bulb.hamiltonians_from_flux, Bulb.nunu_from_flux
+_vac, _matter = ph.vacuum_hamiltonian, ph.matter_strength
+
+PINS = {
+    "vacuum_rk4": lambda: pins.test_vacuum_closed_form("rk4"),
+    "vacuum_dp45": lambda: pins.test_vacuum_closed_form("dp45"),
+    "msw_normal": lambda: pins.test_constant_matter_closed_form(1.0),
+    "msw_inverted": lambda: pins.test_constant_matter_closed_form(-1.0),
+    "antineutrino": pins.test_antineutrino_conjugated_convention,
+    "single_angle": pins.test_single_angle_geometric_factor,
+    "lepton_number": pins.test_lepton_number_invariant,
+    "synchronised": pins.test_synchronised_precession,
+    "four_psi": lambda: pins.test_four_wavefunctions_equal_reduced_state(2),
+    "three_to_two": pins.test_three_flavours_reduce_to_two,
+    "library_rk": pins.test_runge_kutta_agrees_with_library_integrator,
+    "trace_purity": pins.test_runge_kutta_trace_exact_purity_to_order,
+    "order_rk4": lambda: pins.test_convergence_order("rk4", 4),
+    "order_dp5": lambda: pins.test_convergence_order("dp5", 5),
+    "controller": pins.test_adaptive_controller_meets_tolerance,
+}
+
+
+# --- the planted mistakes ---------------------------------------------------------------------------
+def vacuum_sign(mp):
+    """H_vac with the opposite sign (Delta m^2 sign convention slip)."""
+    mp.setattr(ph, "vacuum_hamiltonian", lambda *a, **k: -_vac(*a, **k))
+
+
+def no_path_factor(mp):
+    """d/dr instead of d/dl: the 1/cos theta of Eq. eom dropped."""
+    mp.setattr(Bulb, "rhs", lambda self, r, Y: _rhs(self, r, Y) * self.cos_theta(r)[None, :, None, None, None])
+
+
+def antineutrino_matter_sign(mp):
+    """Antineutrinos given +H_mat instead of -H_mat."""
+    def hff(self, r, F):
+        H, Hbar = _hff(self, r, F)
+        return H, Hbar + 2.0 * ph.matter_strength(r, self.wl) * self.Pe
+    mp.setattr(Bulb, "hamiltonians_from_flux", hff)
+
+
+def commutator_order(mp):
+    """-i [rho, H] instead of -i [H, rho]."""
+    mp.setattr(Bulb, "rhs", lambda self, r, Y: -_rhs(self, r, Y))
+
+
+def antineutrino_nunu_not_conjugated(mp):
+    """Antineutrinos given -H_nunu instead of -H_nunu^*."""
+    def hff(self, r, F):
+        H, Hbar = _hff(self, r, F)
+        Hnn = self.nunu_from_flux(r, F)[:, None]
+        return H, Hbar + np.conj(Hnn) - Hnn
+    mp.setattr(Bulb, "hamiltonians_from_flux", hff)
+
+
+def _nunu(self, r, F, measure_cos=True, beam_cos=True):
+    Fsum = F.sum(axis=1)
+    c = self.cos_theta(r)
+    w = self.grid.du * self.wl.R_km**2 / (2.0 * r * r * (c if measure_cos else 1.0))
+    Phi1 = np.einsum("j,jab->ab", w, Fsum)
+    Phic = np.einsum("j,jab->ab", w * c, Fsum)
+    cb = c[:, None, None] if beam_cos else np.ones((len(c), 1, 1))
+    return self.K * (Phi1[None] - cb * Phic[None])
+
+
+def nunu_without_beam_cosine(mp):
+    """1 - v.v' with the beam's own cos theta dropped: Phi_1 - Phi_c for every beam."""
+    mp.setattr(Bulb, "nunu_from_flux",
+               lambda self, r, F: _nff(self, r, F) if self.geometry == "homogeneous" else _nunu(self, r, F, beam_cos=False))
+
+
+def measure_without_cosine(mp):
+    """d(cos theta') = R^2/(2 r^2) du, the 1/cos theta' of the u-bin measure dropped."""
+    mp.setattr(Bulb, "nunu_from_flux",
+               lambda self, r, F: _nff(self, r, F) if self.geometry == "homogeneous" else _nunu(self, r, F, measure_cos=False))
+
+
+def flux_antineutrino_sign(mp):
+    """F = rho_nu + rho_nubar^* instead of rho_nu - rho_nubar^*."""
+    def flux(self, P, Pbar):
+        N = self.grid.N
+        I = np.eye(self.n, dtype=np.complex128)
+        Ne, Nx = N[0, 0][None, :, None, None], N[0, 1][None, :, None, None]
+        Nbe, Nbx = N[1, 0][None, :, None, None], N[1, 1][None, :, None, None]
+        return (Ne * P + Nx * (I - P)) + np.conj(Nbe * Pbar + Nbx * (I - Pbar))
+    mp.setattr(Bulb, "flux_matrices", flux)
+
+
+def matter_factor_two(mp):
+    """lambda(r) twice too large (a factor slip in sqrt(2) G_F n_e)."""
+    mp.setattr(ph, "matter_strength", lambda r, wl: 2.0 * _matter(r, wl))
+
+
+def cos_theta_unsquared(mp):
+    """cos theta = sqrt(1 - u R/r): the square of R/r dropped."""
+    mp.setattr(ph, "cos_theta", lambda u, R, r: np.sqrt(1.0 - u * R / r))
+
+
+def rk4_equal_weights(mp):
+    """RK4 with weights 1/4 instead of 1/6, 1/3, 1/3, 1/6."""
+    def rk4(f, r, Y, h):
+        k1 = f(r, Y)
+        k2 = f(r + 0.5 * h, Y + (0.5 * h) * k1)
+        k3 = f(r + 0.5 * h, Y + (0.5 * h) * k2)
+        k4 = f(r + h, Y + h * k3)
+        return Y + h * (k1 + k2 + k3 + k4) / 4
+    mp.setattr(ig, "rk4_step", rk4)
+
+
+def dormand_prince_weight(mp):
+    """b_3 = 500/1112 instead of 500/1113 in the Dormand-Prince tableau."""
+    b = ig.DP_B.copy()
+    b[2] = 500.0 / 1112.0
+    mp.setattr(ig, "DP_B", b)
+
+
+CASES = [
+    (vacuum_sign, ["msw_normal", "msw_inverted", "synchronised"]),
+    (no_path_factor, ["vacuum_rk4", "antineutrino", "lepton_number"]),
+    (antineutrino_matter_sign, ["msw_normal", "msw_inverted", "antineutrino"]),
+    (commutator_order, ["antineutrino", "synchronised"]),
+    (antineutrino_nunu_not_conjugated, ["antineutrino", "lepton_number", "synchronised"]),
+    (nunu_without_beam_cosine, ["lepton_number"]),
+    (measure_without_cosine, ["single_angle", "lepton_number"]),
+    (flux_antineutrino_sign, ["synchronised", "four_psi"]),
+    (matter_factor_two, ["msw_normal", "msw_inverted", "antineutrino"]),
+    (cos_theta_unsquared, ["vacuum_rk4", "single_angle", "three_to_two", "trace_purity"]),
+    (rk4_equal_weights, ["vacuum_rk4", "library_rk", "order_rk4", "trace_purity"]),
+    (dormand_prince_weight, ["vacuum_dp45", "order_dp5", "controller"]),
+]
+
+
+@pytest.mark.parametrize("mistake,catchers", CASES, ids=[m.__name__ for m, _ in CASES])
+def test_pins_catch_planted_mistake(monkeypatch, mistake, catchers):
+    mistake(monkeypatch)
+    missed = []
+    for name in catchers:
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")
+            try:
+                PINS[name]()
+            except (AssertionError, FloatingPointError, ValueError, np.linalg.LinAlgError):
+                continue
+        missed.append(name)
+    assert not missed, f"{mistake.__name__} passed the pins {missed}"
