@@ -8,7 +8,9 @@ import warnings
 import numpy as np
 import pytest
 
+import test_oracle_extended as ext_pins
 import test_oracle_pins as pins
+from oracle import extended as ex
 from oracle import integrate as ig
 from oracle import physics as ph
 
@@ -156,5 +158,69 @@ def test_pins_catch_planted_mistake(monkeypatch, mistake, catchers):
                 PINS[name]()
             except (AssertionError, FloatingPointError, ValueError, np.linalg.LinAlgError):
                 continue
+        missed.append(name)
+    assert not missed, f"{mistake.__name__} passed the pins {missed}"
+
+
+# --- the extended bulb model (azimuthal bins, Eq. F with the measure of Eq. int-v) ---------------------
+EXT_PINS = {
+    "axial_symmetry": ext_pins.test_axial_symmetry_reduces_to_bulb,
+    "shift_symmetry": ext_pins.test_azimuthal_shift_symmetry,
+    "cos_phi_moment": ext_pins.test_cos_phi_modulation_moments,
+}
+
+
+def _ext_moments(self, r, F, per_bin=True, sc_weight="cos"):
+    Fsum = F.sum(axis=2)
+    c = self.cos_theta(r)
+    s = np.sqrt(1.0 - c * c)
+    w = self.grid.du * self.wl.R_km**2 / (2.0 * r * r * c) / (self.n_phi if per_bin else 1)
+    cp, sp = np.cos(self.phi), np.sin(self.phi)
+    Phi1 = np.einsum("j,jpab->ab", w, Fsum)
+    Phic = np.einsum("j,jpab->ab", w * c, Fsum)
+    Phisc = np.einsum("j,p,jpab->ab", w * s, cp if sc_weight == "cos" else sp, Fsum)
+    Phiss = np.einsum("j,p,jpab->ab", w * s, sp, Fsum)
+    return Phi1, Phic, Phisc, Phiss
+
+
+def azimuthal_measure_without_bins(mp):
+    """The phi integral without its 1/(2 pi): weights du instead of du / n_phi."""
+    mp.setattr(ex.ExtendedBulb, "moments", lambda self, r, F: _ext_moments(self, r, F, per_bin=False))
+
+
+def cos_moment_with_sine_weight(mp):
+    """Phi_sc weighted by sin phi' instead of cos phi'."""
+    mp.setattr(ex.ExtendedBulb, "moments", lambda self, r, F: _ext_moments(self, r, F, sc_weight="sin"))
+
+
+def sine_term_sign(mp):
+    """sin th (cos phi Phi_sc - sin phi Phi_ss): the sign of the sin phi sin phi' term flipped."""
+    def nunu(self, r, F):
+        Phi1, Phic, Phisc, Phiss = self.moments(r, F)
+        c = self.cos_theta(r)
+        s = np.sqrt(1.0 - c * c)
+        cp, sp = np.cos(self.phi), np.sin(self.phi)
+        return self.K * (Phi1[None, None] - c[:, None, None, None] * Phic[None, None]
+                         - s[:, None, None, None] * (cp[None, :, None, None] * Phisc[None, None]
+                                                     - sp[None, :, None, None] * Phiss[None, None]))
+    mp.setattr(ex.ExtendedBulb, "nunu", nunu)
+
+
+EXT_CASES = [
+    (azimuthal_measure_without_bins, ["axial_symmetry"]),
+    (cos_moment_with_sine_weight, ["cos_phi_moment"]),
+    (sine_term_sign, ["shift_symmetry"]),
+]
+
+
+@pytest.mark.parametrize("mistake,catchers", EXT_CASES, ids=[m.__name__ for m, _ in EXT_CASES])
+def test_extended_pins_catch_planted_mistake(monkeypatch, mistake, catchers):
+    mistake(monkeypatch)
+    missed = []
+    for name in catchers:
+        try:
+            EXT_PINS[name]()
+        except AssertionError:
+            continue
         missed.append(name)
     assert not missed, f"{mistake.__name__} passed the pins {missed}"
