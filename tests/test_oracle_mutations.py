@@ -8,8 +8,10 @@ import warnings
 import numpy as np
 import pytest
 
+import test_oracle_adjoint as adj_pins
 import test_oracle_extended as ext_pins
 import test_oracle_pins as pins
+from oracle import adjoint as adj
 from oracle import extended as ex
 from oracle import integrate as ig
 from oracle import physics as ph
@@ -224,3 +226,32 @@ def test_extended_pins_catch_planted_mistake(monkeypatch, mistake, catchers):
             continue
         missed.append(name)
     assert not missed, f"{mistake.__name__} passed the pins {missed}"
+
+
+# --- the discrete adjoint ------------------------------------------------------------------------------
+_vjp = adj.rhs_vjp
+
+
+def adjoint_mixing_angle_sign(mp):
+    """d(H_vac)/d(theta_v) with the wrong sign in the adjoint of one right-hand-side evaluation."""
+    def vjp(*a, **k):
+        G_Y, G_N, G_th = _vjp(*a, **k)
+        return G_Y, G_N, -G_th
+    mp.setattr(adj, "rhs_vjp", vjp)
+
+
+def adjoint_luminosity_transposed(mp):
+    """The luminosity gradient of nu and nubar swapped."""
+    def vjp(*a, **k):
+        G_Y, G_N, G_th = _vjp(*a, **k)
+        return G_Y, G_N[::-1].copy(), G_th
+    mp.setattr(adj, "rhs_vjp", vjp)
+
+
+@pytest.mark.parametrize("mistake", [adjoint_mixing_angle_sign, adjoint_luminosity_transposed],
+                         ids=["adjoint_mixing_angle_sign", "adjoint_luminosity_transposed"])
+def test_adjoint_pin_catches_planted_mistake(monkeypatch, mistake):
+    mistake(monkeypatch)
+    kw, win, n = adj_pins.CASES[0]
+    with pytest.raises(AssertionError):
+        adj_pins.test_adjoint_matches_central_differences(kw, win, n)
