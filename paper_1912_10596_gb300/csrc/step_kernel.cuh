@@ -540,7 +540,7 @@ __device__ __forceinline__ double controller_factor(double err) {
     double yp = y;
 #pragma unroll
     for (int q = 1; q < P; ++q) yp *= y;
-    y = y * fma(-err / P, yp, (P + 1.0) / P);
+    y = y * fma(err * (-1.0 / P), yp, (P + 1.0) / P);
   }
   return 0.9 * y;
 }
@@ -634,6 +634,7 @@ __device__ int serial_update(const KParams& p, int slot, bool final_pass, bool i
     int last = __ldcg(&d.last), parity = __ldcg(&d.parity);
     unsigned long long accepted = __ldcg(&d.accepted), rejected = __ldcg(&d.rejected);
     unsigned long long evals = __ldcg(&d.stage_evals);
+    const double h_min = ic.h_min, h_max = ic.h_max;
     if (done || status) continue;
     if (nonfin) {
       d.status = 5;  // XFLAT_ERR_NONFINITE
@@ -701,8 +702,8 @@ __device__ int serial_update(const KParams& p, int slot, bool final_pass, bool i
         rejected += 1;
       }
       const double fac = ok ? fmin(5.0, fmax(0.2, q)) : fmax(0.2, q);
-      hh = fmin(hh * fac, ic.h_max);
-      if (!fin && hh < ic.h_min) {
+      hh = fmin(hh * fac, h_max);
+      if (!fin && hh < h_min) {
         d.status = 6;  // XFLAT_ERR_STEP
         atomicCAS(p.status, 0, 6);
         step_err = true;
@@ -847,6 +848,7 @@ struct BlockShared {
   int parity;
   int flag;
   int pass_idx;                        // passes run by this block in this launch (pass trace)
+  int keep;                            // single-piece block: launch-invariant set-up already loaded
   unsigned int gen_seen;               // barrier generation this block arrived in
 };
 
@@ -1421,7 +1423,8 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
   // A block with a single piece keeps its set-up in shared memory for the whole step: after pass
   // 0 only the newest stage's constants and the table rows of the newest and the formed stage
   // change (flags, step size, coefficients, radii, angle tables and older rows stay valid).
-  const bool incremental = (b1 - b0 == 1) && kNewest >= 1;
+  const bool single = b1 - b0 == 1;
+  const bool incremental = single && kNewest >= 1;
   for (int pi = b0; pi < b1; ++pi) {
     const Piece pc = p.pieces[pi];
     const InstConst& ic = p.ic[pc.inst];
@@ -1501,21 +1504,26 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       bs.hB2[i] = pk(fb, fb);
       bs.hE2[i] = pk(fe, fe);
     }
-    if (threadIdx.x < 6) {
-      bs.vac[threadIdx.x] = (Real)ic.M21[threadIdx.x];
-      bs.vac[6 + threadIdx.x] = (Real)ic.M31[threadIdx.x];
-    }
-    if (threadIdx.x == 0) {
-      bs.rtol = (Real)ic.rtol;
-      bs.atol = (Real)ic.atol;
-    }
-    for (int t = threadIdx.x; t < (int)pc.n_jj; t += blockDim.x) {
-      const int jj = pc.jj_lo + t;
-      const int j = jj >= (int)ic.n_angle ? jj - (int)ic.n_angle : jj;
-      dut[t] = (Real)p.du_tab[ic.a_off + j];
-      ut[t] = p.u_tab[ic.a_off + j];
+    // launch-invariant part (vacuum matrices, tolerances, angle tables): a single-piece block
+    // loads it once per launch
+    if (!(single && bs.keep)) {
+      if (threadIdx.x < 6) {
+        bs.vac[threadIdx.x] = (Real)ic.M21[threadIdx.x];
+        bs.vac[6 + threadIdx.x] = (Real)ic.M31[threadIdx.x];
+      }
+      if (threadIdx.x == 0) {
+        bs.rtol = (Real)ic.rtol;
+        bs.atol = (Real)ic.atol;
+      }
+      for (int t = threadIdx.x; t < (int)pc.n_jj; t += blockDim.x) {
+        const int jj = pc.jj_lo + t;
+        const int j = jj >= (int)ic.n_angle ? jj - (int)ic.n_angle : jj;
+        dut[t] = (Real)p.du_tab[ic.a_off + j];
+        ut[t] = p.u_tab[ic.a_off + j];
+      }
     }
     __syncthreads();
+    if (single && threadIdx.x == 0) bs.keep = 1;     // read after later barriers only
     }
     const int n_jj = pc.n_jj;
     if (!bs.active) continue;
@@ -1835,6 +1843,7 @@ __global__ void __launch_bounds__(kThreads, kMinB) step_kernel(KParams p) {
   __shared__ BlockShared<Real, Phys> bs;
   if (threadIdx.x == 0) {
     bs.pass_idx = 0;
+    bs.keep = 0;
     bs.gen_seen = ld_acquire(&p.bar->gen);        // later barriers track the generation locally
   }
   if (p.init_only) {
