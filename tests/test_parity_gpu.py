@@ -162,6 +162,37 @@ def test_mixed_precision_against_fp64_oracle(xf, shape):
     assert abs(mean - Bulb(wl).mean_survival(Y)) < 1e-4
 
 
+def test_mixed_three_flavours_against_fp64_oracle(xf):
+    """Three flavours in mixed precision (FP32 density matrices, FP64 moments and control):
+    survival probabilities within 1e-4 of the FP64 oracle through a window with evolution."""
+    wl = Workload(name="m3", n_flavor=3, n_energy=13, n_angle=11, dm2=(7.5e-5, 2.4e-3),
+                  theta=(0.59, 0.15, 0.785), integrator="dp45", rtol=1e-9, atol=1e-9, h0=1e-3)
+    Y, st = oracle_run(wl, Bulb(wl).initial_state(), 100.0, 103.0)
+    s = make_solver(xf, wl, precision="mixed", rtol=1e-6, atol=1e-6)
+    s.reset(100.0)
+    s.evolve(100.0, 103.0)
+    pee, _ = s.pee()
+    ref = beams(Y)[:, 0, 0].real
+    assert np.abs(ref - 1).max() > 1e-2
+    assert np.abs(pee - ref).max() < 1e-4
+
+
+def test_mixed_fixed_step_rk4_against_fp64_oracle(xf):
+    """Two flavours, mixed precision, fixed-step RK4 (the FP32 pair kernels' RK4 tableau): the same
+    200 steps as the oracle's FP64 run, survival probabilities within 1e-4."""
+    wl = Workload(name="mr", **RAGGED, integrator="rk4", n_steps=200)
+    r0, r1 = 100.0, 110.0
+    s = make_solver(xf, wl, precision="mixed", fixed_dr_km=(r1 - r0) / wl.n_steps)
+    s.reset(r0)
+    s.evolve(r0, r1)
+    Y, _ = oracle_run(wl, Bulb(wl).initial_state(), r0, r1)
+    pee, _ = s.pee()
+    ref = beams(Y)[:, 0, 0].real
+    assert np.abs(ref - 1).max() > 0.5
+    assert np.abs(pee - ref).max() < 1e-4
+    assert s.stats().accepted == 200
+
+
 def test_bitwise_deterministic(xf):
     wl = Workload(name="det", **RAGGED, integrator="dp45", h0=1e-3)
     outs = []
