@@ -7,7 +7,7 @@ import pytest
 from bulb_inputs import Workload, random_unit_states
 from oracle.physics import Bulb
 from oracle.extended import ExtendedBulb
-from oracle.integrate import evolve_fixed, evolve_adaptive
+from oracle.integrate import evolve_fixed, evolve_adaptive, evolve_em2
 from parity_util import beams, rel_err, make_solver
 
 pytestmark = pytest.mark.gpu
@@ -41,19 +41,22 @@ def test_extended_moments_match_oracle(xf):
     assert np.abs(Rc).max() > 1e-3 * np.abs(R1).max()
 
 
-@pytest.mark.parametrize("integrator", ["rk4", "dp45"])
+@pytest.mark.parametrize("integrator", ["rk4", "dp45", "lie_rk4", "exp_midpoint"])
 def test_extended_parity_asymmetric(xf, integrator):
-    wl = Workload(name="ex", **SIZES, integrator=integrator, n_steps=40, h0=0.5)
+    # the second-order exponential midpoint rule runs at rtol = atol = 1e-6 (~700 steps per km)
+    tol = 1e-6 if integrator == "exp_midpoint" else 1e-9
+    wl = Workload(name="ex", **SIZES, integrator=integrator, n_steps=40, h0=0.5, rtol=tol, atol=tol)
     eb = ExtendedBulb(wl, NPHI)
     Y0 = asym_state(eb, 7)
     r0, r1 = 100.0, 101.0
     s = make_solver(xf, wl, n_phi=NPHI, fixed_dr_km=(r1 - r0) / 40)
     s.set_rho(beams(Y0), r0)
     s.evolve(r0, r1)
-    if integrator == "rk4":
-        Y, _ = evolve_fixed(eb, Y0, r0, r1, 40)
+    if integrator in ("rk4", "lie_rk4"):
+        Y, _ = evolve_fixed(eb, Y0, r0, r1, 40, integrator)
     else:
-        Y, _, st = evolve_adaptive(eb, Y0, r0, r1, wl.rtol, wl.atol, wl.h0)
+        evolve = evolve_adaptive if integrator == "dp45" else evolve_em2
+        Y, _, st = evolve(eb, Y0, r0, r1, wl.rtol, wl.atol, wl.h0)
         gs = s.stats()
         assert (gs.accepted, gs.rejected) == (st.accepted, st.rejected)
     assert rel_err(beams(Y), beams(Y0)) > 1e-3
