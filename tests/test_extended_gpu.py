@@ -92,3 +92,25 @@ def test_extended_mixed_against_fp64_oracle(xf):
     pee, _ = s.pee()
     ref = beams(Y)[:, 0, 0].real
     assert np.abs(pee - ref).max() < 1e-4
+
+
+@pytest.mark.parametrize("integrator", ["rk4", "lie_rk4", "exp_midpoint"])
+def test_extended_mixed_other_integrators(xf, integrator):
+    """The mixed extended kernels of the fixed-step and exponential integrators against the FP64
+    oracle's same scheme: survival probabilities within 1e-4."""
+    tol = 1e-6 if integrator == "exp_midpoint" else 1e-9
+    wl = Workload(name="exm2", **SIZES, integrator=integrator, n_steps=40, h0=1e-2, rtol=tol, atol=tol)
+    eb = ExtendedBulb(wl, NPHI)
+    Y0 = asym_state(eb, 13)
+    r0, r1 = 100.0, 101.0
+    if integrator == "exp_midpoint":
+        Y, _, _ = evolve_em2(eb, Y0, r0, r1, tol, tol, 1e-2)
+    else:
+        Y, _ = evolve_fixed(eb, Y0, r0, r1, 40, integrator)
+    s = make_solver(xf, wl, n_phi=NPHI, precision="mixed", fixed_dr_km=(r1 - r0) / 40)
+    s.set_rho(beams(Y0), r0)
+    s.evolve(r0, r1)
+    pee, _ = s.pee()
+    ref = beams(Y)[:, 0, 0].real
+    assert np.abs(ref - beams(Y0)[:, 0, 0].real).max() > 1e-3
+    assert np.abs(pee - ref).max() < 1e-4

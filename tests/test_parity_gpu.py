@@ -193,6 +193,21 @@ def test_mixed_fixed_step_rk4_against_fp64_oracle(xf):
     assert s.stats().accepted == 200
 
 
+def test_mixed_lie_rk4_against_fp64_oracle(xf):
+    """Two flavours, mixed precision, commutator-free Lie RK4 (FP32 rotations): the same 200
+    steps as the oracle's FP64 run, survival probabilities within 1e-4."""
+    wl = Workload(name="ml", **RAGGED, integrator="lie_rk4", n_steps=200)
+    r0, r1 = 100.0, 110.0
+    s = make_solver(xf, wl, precision="mixed", fixed_dr_km=(r1 - r0) / wl.n_steps)
+    s.reset(r0)
+    s.evolve(r0, r1)
+    Y, _ = oracle_run(wl, Bulb(wl).initial_state(), r0, r1)
+    pee, _ = s.pee()
+    ref = beams(Y)[:, 0, 0].real
+    assert np.abs(ref - 1).max() > 0.5
+    assert np.abs(pee - ref).max() < 1e-4
+
+
 def test_bitwise_deterministic(xf):
     wl = Workload(name="det", **RAGGED, integrator="dp45", h0=1e-3)
     outs = []
