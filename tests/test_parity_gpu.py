@@ -162,13 +162,15 @@ def test_mixed_precision_against_fp64_oracle(xf, shape):
     assert abs(mean - Bulb(wl).mean_survival(Y)) < 1e-4
 
 
-def test_mixed_three_flavours_against_fp64_oracle(xf):
+@pytest.mark.parametrize("integrator", ["dp45", "rk4"])
+def test_mixed_three_flavours_against_fp64_oracle(xf, integrator):
     """Three flavours in mixed precision (FP32 density matrices, FP64 moments and control):
     survival probabilities within 1e-4 of the FP64 oracle through a window with evolution."""
     wl = Workload(name="m3", n_flavor=3, n_energy=13, n_angle=11, dm2=(7.5e-5, 2.4e-3),
-                  theta=(0.59, 0.15, 0.785), integrator="dp45", rtol=1e-9, atol=1e-9, h0=1e-3)
+                  theta=(0.59, 0.15, 0.785), integrator=integrator, n_steps=300, rtol=1e-9,
+                  atol=1e-9, h0=1e-3)
     Y, st = oracle_run(wl, Bulb(wl).initial_state(), 100.0, 103.0)
-    s = make_solver(xf, wl, precision="mixed", rtol=1e-6, atol=1e-6)
+    s = make_solver(xf, wl, precision="mixed", rtol=1e-6, atol=1e-6, fixed_dr_km=3.0 / 300)
     s.reset(100.0)
     s.evolve(100.0, 103.0)
     pee, _ = s.pee()
