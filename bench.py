@@ -15,6 +15,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -33,19 +34,29 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM traffic of one timed launch of the step kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of an 8-step launch after the L2 flush,
 # profiles/step_kernel_mixed_dp45_4M.md).  It holds only for that launch size and for the kernel
-# sources it was taken on, identified by their SHA-256; otherwise the benchmark reports null.
+# code it was taken on, identified by kernel_code_hash(); otherwise the benchmark reports null.
 STEP_TRAFFIC = {"bytes_per_launch": 51211776 + 180451072, "steps_per_launch": 8,
-                "sources_sha256": "8818cb8b4f5169d3c53f9ac9355964b2cd401f9765317f59acf2e25959de1cac"}
+                "code_sha256": "79f035ee32042e38ee4472565b6a26051ef80ea2323ca7713b4b3ebc5e9ac1ec"}
 KERNEL_SOURCES = ["step_kernel.cuh", "xflat_internal.cuh", "kernels_2f.cu"]
 
 
-def step_traffic(steps_per_launch):
+def kernel_code_hash():
+    """SHA-256 of the step kernel's code: the sources with comments and blank lines removed, so a
+    comment edit does not invalidate the recorded counters but any code change does."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1912_10596_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    ok = h.hexdigest() == STEP_TRAFFIC["sources_sha256"] and steps_per_launch == STEP_TRAFFIC["steps_per_launch"]
+        with open(os.path.join(ROOT, "paper_1912_10596_gb300", "csrc", f)) as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in text.splitlines():
+            code = line.split("//", 1)[0].strip()
+            if code:
+                h.update(code.encode() + b"\n")
+    return h.hexdigest()
+
+
+def step_traffic(steps_per_launch):
+    ok = kernel_code_hash() == STEP_TRAFFIC["code_sha256"] and steps_per_launch == STEP_TRAFFIC["steps_per_launch"]
     return STEP_TRAFFIC["bytes_per_launch"] if ok else None
 METRIC = "beam-updates/s (beams x RK stages)"
 

@@ -4,15 +4,17 @@
 // sequence of passes over all beams separated by device-wide barriers, because every stage of the
 // integrator needs the angular moments of *all* beams (Eq. Hnu / Eq. F):
 //
-//   pass p (p = 0 .. S-2): rebuild the stage state Y_{p+2} of every beam from the step's initial
-//       state y and the stage constants of the earlier stages (the stage derivatives k_1..k_{p+1}
-//       are recomputed in registers instead of being stored), and reduce the moments of Y_{p+2};
-//   final pass: rebuild the chain once more, form the new state (and, for DP45, the embedded error),
-//       write it to the second state buffer and reduce either the moments of the new state (fixed
-//       step) or the error norm (DP45).
+//   pass p (p = 0 .. S-2): form the stage state Y_{p+2} of every beam from the step's initial
+//       state y and the stage derivatives k_1..k_{p+1}, and reduce the moments of Y_{p+2}.  FP32
+//       kernels recompute k_1..k_{p+1} in registers from y and the earlier stages' constants (the
+//       stage vectors are not stored); FP64 RK4 / DP45 kernels read k_1..k_p and Y_{p+1} back from
+//       HBM planes and evaluate only k_{p+1} (stored_stages);
+//   final pass: form the new state (and, for DP45, the embedded error), write it to the second
+//       state buffer and reduce either the moments of the new state (fixed step) or the error norm
+//       (DP45).
 //
-// So every pass reads each beam's state once (128-bit vector loads of the SoA planes) and a step
-// writes it once.
+// So every pass reads each beam's state once (vector loads of the SoA planes) and a step writes it
+// once; the FP64 kernels also move their stage planes.
 //
 // Moments without cancellation.  With the measure of Eq. Hnu in u-bins, the nu-nu term of beam b is
 // mu(r) (J0 - cos(th_b) J1), J0 = sum w s / cos(th), J1 = sum w s.  Far from the neutrino sphere
