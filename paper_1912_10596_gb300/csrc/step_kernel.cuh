@@ -901,9 +901,9 @@ template <class Phys, class Tab, typename Real, int kPass, int kKind>
 struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
   static constexpr int NC = Phys::NC;
   static constexpr bool kSplit = split_final<Tab, Real>();
-  // number of stage derivatives to rebuild before the stage state of this pass (split final pass:
-  // none, the pass forming Y_S left y5 and the error partial behind; unsplit adaptive: S - 1, k_S
-  // follows from the new state)
+  // number of stage derivatives the pass needs before its stage state, rebuilt or (stored stages)
+  // read back (split final pass: none, the pass forming Y_S left y5 and the error partial behind;
+  // unsplit adaptive: S - 1, k_S follows from the new state)
   static constexpr int kChain =
       kKind == kInitPass ? 0
       : (kKind == kFinalPass ? (kSplit ? 0 : Tab::S - (Tab::kAdaptive ? 1 : 0)) : kPass + 1);
