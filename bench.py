@@ -501,7 +501,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "beam-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 per-beam + f64 reductions", "data": "synthetic",
+            "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "beams": wl.n_beams, "integrator": "dp45",
                        "precision": "mixed", "r_start_km": 11.0, "stage_evals_per_step": bsu / wl.n_beams,
                        "steps_per_launch": spl,
