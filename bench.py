@@ -503,7 +503,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "beams": wl.n_beams, "integrator": "dp45",
-                       "precision": "mixed", "r_start_km": 11.0, "stage_evals_per_step": bsu / wl.n_beams,
+                       "precision": "mixed: f32 per-beam algebra, f64 moment reductions and step control",
+                       "r_start_km": 11.0, "stage_evals_per_step": bsu / wl.n_beams,
                        "steps_per_launch": spl,
                        "l2": f"flushed before every timed launch of up to {spl} steps (write of a 258 MB buffer)",
                        "grid_blocks": st.grid_blocks, "block_size": st.block_size,
