@@ -275,13 +275,15 @@ def measure_configs(only=None):
     * 64 batched instances (mixed DP45, about 29 M beams): a window of steps from 11 km, one
       persistent launch per chunk for all instances;
     * adjoint (200 E x 400 u, FP64 RK4, 5000 steps over 100 -> 300 km, checkpoints every 64 steps):
-      time per gradient."""
+      time per gradient;
+    * extended bulb model, 100 E x 10 phi x 2000 u (4M beams, mixed DP45): a window of steps."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__ as g
     g.build()
     from paper_1912_10596_gb300 import xflat as xf
-    from bulb_inputs import workload_2f_small_fp64, workload_3f_fp64, batched_workloads, workload_adjoint
+    from bulb_inputs import (Workload, workload_2f_small_fp64, workload_3f_fp64, batched_workloads,
+                             workload_adjoint)
     stream = torch.cuda.current_stream()
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     hbm, peak_kind = _peaks()
@@ -369,6 +371,18 @@ def measure_configs(only=None):
              window="16 DP45 steps of every instance from 11 km", state_bytes=12 * total,
              block_size=sv.stats().block_size, blocks=sv.stats().grid_blocks)
         sv.close()
+    # extended bulb model in the shape of the paper's runs (energies x azimuthal x polar bins,
+    # Sec. 4.2): 100 E x 10 phi x 2000 u x (nu, nubar) = 4M beams, mixed DP45, four moments
+    if want("extended"):
+        wl = Workload(name="bulb2f_ext_100E_10phi_2000u_mixed_dp45", n_energy=100, n_angle=2000,
+                      matter="power_law", r0=11.0, r1=500.0, integrator="dp45", precision="mixed",
+                      rtol=1e-6, atol=1e-6)
+        sv = solver([xf.config_from_workload(wl, n_phi=10)], [wl.spectra()])
+        ms, bsu = window(sv, [wl.r1], 16)
+        nb = sv.nbeams()
+        line(wl.name, nb, bsu, ms, 16, 14.0, window="16 DP45 steps from 11 km",
+             block_size=sv.stats().block_size, blocks=sv.stats().grid_blocks)
+        sv.close()
     if not want("adjoint"):
         return
 
@@ -405,7 +419,7 @@ def main():
                     help="accuracy against cost of the integrators on the 4096-beam case instead of the benchmark")
     ap.add_argument("--configs", action="store_true",
                     help="device rates of the other workloads (small, three-flavour, batched, adjoint) instead of the benchmark")
-    ap.add_argument("--only", choices=["small", "3f", "batched", "adjoint"],
+    ap.add_argument("--only", choices=["small", "3f", "batched", "extended", "adjoint"],
                     help="with --configs: measure one of the workloads")
     args = ap.parse_args()
     if args.compare_integrators:
