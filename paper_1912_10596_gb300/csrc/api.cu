@@ -444,10 +444,11 @@ void build_pieces(xflat_t h, int G) {
 // Values per (stage, angle bin) table row of the step kernel (Phys2<float>::KT, Phys2<double>::KT,
 // Phys3::KT), and the cap on angle bins per piece that bounds the table's shared memory.
 int table_row_values(int nf, size_t real_size, bool ext = false) {
-  return ext ? 10 : (nf == 2 ? (real_size == 4 ? 24 : 8) : 4);
+  if (ext) return real_size == 4 ? 28 : 10;
+  return nf == 2 ? (real_size == 4 ? 24 : 8) : 4;
 }
-uint32_t max_jj_cap(int nf, size_t real_size, bool ext) {
-  return (nf == 2 && real_size == 4 && !ext) ? 64u : kMaxJJ;
+uint32_t max_jj_cap(int nf, size_t real_size, bool) {
+  return (nf == 2 && real_size == 4) ? 64u : kMaxJJ;     // FP32 pair rows are the widest
 }
 
 size_t smem_bytes(int nf, size_t real_size, int max_jj, bool ext = false) {

@@ -390,44 +390,82 @@ struct Phys3 {
 // Table row (KT = 10): t1, q, q Bx, q Bz, G0 (3), (sin th / cos th) cos phi, (sin th / cos th) sin phi.
 template <typename Real>
 struct Phys2E {
-  static constexpr bool kPairable = false;
-  static constexpr int NC = 3, NM = 12, NSC = 14, KT = 10;
-  enum : int { vT1 = 0, vQ = 1, vQBX = 2, vQBZ = 3, vG0X = 4, vG0Y = 5, vG0Z = 6, vSCC = 7, vSCS = 8 };
+  static constexpr bool kF32 = sizeof(Real) == 4;
+  static constexpr bool kPairable = kF32;       // FP32 passes run beam pairs (PairRK)
+  static constexpr int NC = 3, NM = 12, NSC = 14, KT = kF32 ? 28 : 10;
+  // the values of a Phys2 row (FP32: each stored twice, negated copies included), then the
+  // azimuthal moment weights (sin th / cos th) cos phi and (sin th / cos th) sin phi
+  enum : int { vT1 = 0, vQ = 1, vQBX = 2, vQBZ = 3, vG0X = 4, vG0Y = 5, vG0Z = 6,
+               vNQBX = 7, vNQBZ = 8, vNG0X = 9, vNG0Y = 10, vNG0Z = 11 };
+  static constexpr int vSCC = kF32 ? 12 : 7, vSCS = kF32 ? 13 : 8;
   struct Consts { double B[3]; int n_phi; };
   using Beam = typename Phys2<Real>::Beam;
 
-  __device__ static inline Real t1(const Real* t) { return t[vT1]; }
+  __device__ static inline Real val(const Real* t, int v) { return kF32 ? t[2 * v] : t[v]; }
+  __device__ static inline void put(Real* t, int v, Real x) {
+    if (kF32) { t[2 * v] = x; t[2 * v + 1] = x; } else { t[v] = x; }
+  }
+  __device__ static inline Real t1(const Real* t) { return val(t, vT1); }
   // sc: mu D (3), mu J1 (3), mu Jc (3), mu Js (3), lambda
-  __device__ static inline void fill_row(Real* t, double u, double x, const double* sc, const Real*,
+  __device__ static inline void fill_row(Real* t, double u, double x, const double* sc, const Real* scr,
                                          const Consts& C, int a, int) {
-    const Geo g = geometry(u, x);
     const int pidx = a % C.n_phi;
-    double sp, cp;
-    sincospi((2.0 * pidx + 1.0) / C.n_phi, &sp, &cp);         // phi_p = 2 pi (p + 1/2) / n_phi
-    const double so = sqrt(u * x) * g.q;                      // sin th / cos th, sin^2 th = u R^2 / r^2
-    t[vT1] = (Real)g.t1;
-    t[vQ] = (Real)g.q;
-    t[vQBX] = (Real)(g.q * C.B[0]);
-    t[vQBZ] = (Real)(g.q * C.B[2]);
+    Real q, t1v, t2, so, sp, cp;
+    if constexpr (kF32) {
+      // FP32 rows in FP32 arithmetic (as Phys2's): the table holds floats anyway, and FP64 square
+      // roots, divisions and sincospi per row would cost more than the row's beams on GB300
+      geometry_f(u, x, q, t1v, t2);
+      so = sqrtf((float)(u * x)) * q;                         // sin th / cos th, sin^2 th = u R^2 / r^2
+      sincospif((2.0f * pidx + 1.0f) / C.n_phi, &sp, &cp);   // phi_p = 2 pi (p + 1/2) / n_phi
+    } else {
+      const Geo g = geometry(u, x);
+      q = g.q;
+      t1v = g.t1;
+      t2 = g.t2;
+      so = sqrt(u * x) * g.q;
+      sincospi((2.0 * pidx + 1.0) / C.n_phi, &sp, &cp);
+    }
+    Real G0[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const double ext = cp * sc[6 + i] + sp * sc[9 + i];
-      t[vG0X + i] = (Real)(g.q * ((i == 2 ? sc[12] : 0.0) + sc[i] + g.t2 * sc[3 + i]) - so * ext);
+      if constexpr (kF32) {
+        const float ext = cp * scr[6 + i] + sp * scr[9 + i];
+        G0[i] = q * ((i == 2 ? scr[12] : 0.0f) + scr[i] + t2 * scr[3 + i]) - so * ext;
+      } else {
+        const double ext = cp * sc[6 + i] + sp * sc[9 + i];
+        G0[i] = q * ((i == 2 ? sc[12] : 0.0) + sc[i] + t2 * sc[3 + i]) - so * ext;
+      }
     }
-    t[vSCC] = (Real)(so * cp);
-    t[vSCS] = (Real)(so * sp);
-    t[9] = 0;
+    const Real qbx = q * (Real)C.B[0], qbz = q * (Real)C.B[2];
+    put(t, vT1, t1v);
+    put(t, vQ, q);
+    put(t, vQBX, qbx);
+    put(t, vQBZ, qbz);
+    put(t, vG0X, G0[0]);
+    put(t, vG0Y, G0[1]);
+    put(t, vG0Z, G0[2]);
+    put(t, vSCC, so * cp);
+    put(t, vSCS, so * sp);
+    if constexpr (kF32) {
+      put(t, vNQBX, -qbx);
+      put(t, vNQBZ, -qbz);
+      put(t, vNG0X, -G0[0]);
+      put(t, vNG0Y, -G0[1]);
+      put(t, vNG0Z, -G0[2]);
+    } else {
+      t[9] = 0;
+    }
   }
   __device__ static inline void K(const Real* t, const Beam& bm, const Real*, const Real*, Real (&Kv)[3]) {
-    Kv[0] = bm.eo * t[vQBX] + t[vG0X];
-    Kv[1] = t[vG0Y];
-    Kv[2] = bm.eo * t[vQBZ] + t[vG0Z];
+    Kv[0] = bm.eo * val(t, vQBX) + val(t, vG0X);
+    Kv[1] = val(t, vG0Y);
+    Kv[2] = bm.eo * val(t, vQBZ) + val(t, vG0Z);
   }
   __device__ static inline void f(const Real (&Kv)[3], const Real (&y)[3], Real (&k)[3]) {
     Phys2<Real>::f(Kv, y, k);
   }
   __device__ static inline void accum_row(Real (&acc)[NM], Real w, const Real* t, const Real (&y)[3]) {
-    const Real wt = w * t[vT1], wc = w * t[vSCC], ws = w * t[vSCS];
+    const Real wt = w * val(t, vT1), wc = w * val(t, vSCC), ws = w * val(t, vSCS);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       acc[i] += wt * y[i];
@@ -1191,9 +1229,9 @@ __device__ __forceinline__ F2 mul2(F2 a, F2 b) {
   return d;
 }
 
-template <class Tab, int kPass, int kKind>
+template <class P, class Tab, int kPass, int kKind>
 struct PairRK {
-  using P = Phys2<float>;
+  static constexpr int NM = P::NM;                 // 6 (bulb) or 12 (extended: + Jc, Js)
   static_assert(!split_final<Tab, float>(), "FP32 passes rebuild the chain in the final pass");
   static constexpr int kChain =
       kKind == kInitPass ? 0 : (kKind == kFinalPass ? Tab::S - (Tab::kAdaptive ? 1 : 0) : kPass + 1);
@@ -1215,10 +1253,17 @@ struct PairRK {
     k[1] = fma2(K[2], Y[0], mul2(nK[0], Y[2]));
     k[2] = fma2(K[0], Y[1], mul2(nK[1], Y[0]));
   }
-  __device__ static inline void accum(F2 (&acc)[6], F2 w, F2 t1, const F2 (&y)[3]) {
-    const F2 wt = mul2(w, t1);
+  // moments of the pair's states with the weights of row R: D (w t1), J1 (w) and, extended model,
+  // Jc (w (sin th / cos th) cos phi), Js (w (sin th / cos th) sin phi)
+  __device__ static inline void accum(F2 (&acc)[NM], F2 w, const F2* R, const F2 (&y)[3]) {
+    const F2 wt = mul2(w, R[P::vT1]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) { acc[i] = fma2(wt, y[i], acc[i]); acc[3 + i] = fma2(w, y[i], acc[3 + i]); }
+    if constexpr (NM == 12) {
+      const F2 wc = mul2(w, R[P::vSCC]), ws = mul2(w, R[P::vSCS]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { acc[6 + i] = fma2(wc, y[i], acc[6 + i]); acc[9 + i] = fma2(ws, y[i], acc[9 + i]); }
+    }
   }
   // 1/sqrt(n2) of a pair: hardware reciprocal square root refined by one Newton step
   // r <- r (3 - n2 r^2) / 2 (relative error ~1e-7, as a correctly rounded quotient would give)
@@ -1242,7 +1287,7 @@ struct PairRK {
   // y, ep as in PassBody::beam
   template <class BS>
   __device__ static inline void run(const BS& bs, F2 eo, F2 w, const F2* rows, int rstride, F2 (&y)[3],
-                                    F2 (&ep)[4], F2 (&acc)[6], float& emax, int& bad) {
+                                    F2 (&ep)[4], F2 (&acc)[NM], float& emax, int& bad) {
     F2 k[Tab::S + 1][3];
     // adaptive final pass: y5 and the error accumulate as soon as each stage derivative exists
     // (same order of operations as summing after the chain), so the derivatives die early
@@ -1276,7 +1321,7 @@ struct PairRK {
       }
     }
     if (kKind == kInitPass) {
-      accum(acc, w, rows[rstride * 1 + P::vT1], y);
+      accum(acc, w, rows + rstride * 1, y);
       return;
     }
     if (kKind == kStagePass) {
@@ -1290,7 +1335,7 @@ struct PairRK {
           for (int i = 0; i < 3; ++i) Y[i] = fma2(ha, k[m][i], Y[i]);
         }
       if (Tab::kAdaptive && I == Tab::S) normalise(Y);
-      accum(acc, w, rows[rstride * I + P::vT1], Y);
+      accum(acc, w, rows + rstride * I, Y);
       return;
     }
     if (Tab::kAdaptive) {
@@ -1356,7 +1401,7 @@ struct PairRK {
     const bool ok0 = 0.5f * (a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]) <= 3.0e38f;
     const bool ok1 = 0.5f * (a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]) <= 3.0e38f;
     if (ok0 && ok1) normalise(yn);
-    accum(acc, w, rows[rstride * Tab::S + P::vT1], yn);
+    accum(acc, w, rows + rstride * Tab::S, yn);
 #pragma unroll
     for (int i = 0; i < 3; ++i) y[i] = yn[i];
   }
@@ -1567,7 +1612,9 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     int bad = 0;
     // FP32 two-flavour RK passes run beam pairs on packed f32x2 arithmetic (PairRK)
     constexpr bool kPair = Phys::kPairable && !kCF;
-    F2 acc2[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    F2 acc2[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) acc2[i] = 0ull;
     float emax2 = 0.0f;
     const uint32_t end = pc.start + pc.len;
     const uint32_t vstep = VN * blockDim.x;
@@ -1619,7 +1666,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
             for (int c = 0; c < 4; ++c) ep2[c] = pk(ep[c][0], ep[c][1]);
           }
           const F2* rows = reinterpret_cast<const F2*>(tab) + (size_t)tj * (Phys::KT / 2);
-          PairRK<Tab, kPass, kKind>::run(bs, pk(b0.eo, b1.eo), pk(b0.w, b1.w), rows,
+          PairRK<Phys, Tab, kPass, kKind>::run(bs, pk(b0.eo, b1.eo), pk(b0.w, b1.w), rows,
                                          n_jj * (Phys::KT / 2), y2, ep2, acc2, emax2, bad);
 #pragma unroll
           for (int c = 0; c < 3; ++c) upk(y2[c], ys[c][0], ys[c][1]);
@@ -1669,7 +1716,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     }
     if constexpr (kPair) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) {
+      for (int i = 0; i < NM; ++i) {
         float a, b;
         upk(acc2[i], a, b);
         acc[i] += a + b;
