@@ -444,11 +444,15 @@ void build_pieces(xflat_t h, int G) {
 // Values per (stage, angle bin) table row of the step kernel (Phys2<float>::KT, Phys2<double>::KT,
 // Phys3::KT), and the cap on angle bins per piece that bounds the table's shared memory.
 int table_row_values(int nf, size_t real_size, bool ext = false) {
-  if (ext) return real_size == 4 ? 28 : 10;
+  if (ext) return real_size == 4 ? 18 : 10;
   return nf == 2 ? (real_size == 4 ? 24 : 8) : 4;
 }
-uint32_t max_jj_cap(int nf, size_t real_size, bool) {
-  return (nf == 2 && real_size == 4) ? 64u : kMaxJJ;     // FP32 pair rows are the widest
+// combined angle rows per piece: bounded by the shared-memory table ([8 stages][rows][row values]);
+// the extended model has ten times the rows per beam, so its rows are kept narrow and a block's
+// share of a 4M-beam problem (about 130 rows at two blocks per SM) fits one piece
+uint32_t max_jj_cap(int nf, size_t real_size, bool ext) {
+  if (nf == 2 && real_size == 4) return ext ? 160u : 64u;
+  return kMaxJJ;
 }
 
 size_t smem_bytes(int nf, size_t real_size, int max_jj, bool ext = false) {

@@ -170,6 +170,7 @@ template <typename Real>
 struct Phys2 {
   static constexpr bool kF32 = sizeof(Real) == 4;
   static constexpr bool kPairable = kF32;       // FP32 passes run beam pairs (PairRK)
+  static constexpr bool kNegated = kF32;        // FP32 rows carry -G0_y (saves a multiply per stage)
   static constexpr int NC = 3, NM = kNM2, NSC = kNSC2, KT = kF32 ? 24 : 8;
   enum : int { vT1 = 0, vQ = 1, vQBX = 2, vQBZ = 3, vG0X = 4, vG0Y = 5, vG0Z = 6,
                vNQBX = 7, vNQBZ = 8, vNG0X = 9, vNG0Y = 10, vNG0Z = 11 };
@@ -392,12 +393,11 @@ template <typename Real>
 struct Phys2E {
   static constexpr bool kF32 = sizeof(Real) == 4;
   static constexpr bool kPairable = kF32;       // FP32 passes run beam pairs (PairRK)
-  static constexpr int NC = 3, NM = 12, NSC = 14, KT = kF32 ? 28 : 10;
-  // the values of a Phys2 row (FP32: each stored twice, negated copies included), then the
-  // azimuthal moment weights (sin th / cos th) cos phi and (sin th / cos th) sin phi
-  enum : int { vT1 = 0, vQ = 1, vQBX = 2, vQBZ = 3, vG0X = 4, vG0Y = 5, vG0Z = 6,
-               vNQBX = 7, vNQBZ = 8, vNG0X = 9, vNG0Y = 10, vNG0Z = 11 };
-  static constexpr int vSCC = kF32 ? 12 : 7, vSCS = kF32 ? 13 : 8;
+  static constexpr bool kNegated = false;       // no negated copies: rows stay small (many rows)
+  static constexpr int NC = 3, NM = 12, NSC = 14, KT = kF32 ? 18 : 10;
+  // t1, q, q Bx, q Bz, G0 (3), then the azimuthal moment weights (sin th / cos th) cos phi and
+  // (sin th / cos th) sin phi; FP32 rows store each value twice (one 64-bit load per packed operand)
+  enum : int { vT1 = 0, vQ = 1, vQBX = 2, vQBZ = 3, vG0X = 4, vG0Y = 5, vG0Z = 6, vSCC = 7, vSCS = 8 };
   struct Consts { double B[3]; int n_phi; };
   using Beam = typename Phys2<Real>::Beam;
 
@@ -446,15 +446,7 @@ struct Phys2E {
     put(t, vG0Z, G0[2]);
     put(t, vSCC, so * cp);
     put(t, vSCS, so * sp);
-    if constexpr (kF32) {
-      put(t, vNQBX, -qbx);
-      put(t, vNQBZ, -qbz);
-      put(t, vNG0X, -G0[0]);
-      put(t, vNG0Y, -G0[1]);
-      put(t, vNG0Z, -G0[2]);
-    } else {
-      t[9] = 0;
-    }
+    if constexpr (!kF32) t[9] = 0;
   }
   __device__ static inline void K(const Real* t, const Beam& bm, const Real*, const Real*, Real (&Kv)[3]) {
     Kv[0] = bm.eo * val(t, vQBX) + val(t, vG0X);
@@ -1244,7 +1236,8 @@ struct PairRK {
     K[1] = R[P::vG0Y];
     K[2] = fma2(eo, R[P::vQBZ], R[P::vG0Z]);
     nK[0] = mul2(K[0], m1);
-    nK[1] = R[P::vNG0Y];
+    if constexpr (P::kNegated) nK[1] = R[P::vNG0Y];
+    else nK[1] = mul2(K[1], m1);
     nK[2] = mul2(K[2], m1);
   }
   // k = K x Y as K1 Y2 - K2 Y1, ... with the products of -K added by FMA
