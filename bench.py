@@ -35,8 +35,8 @@ L2_BYTES = 129 * 1024 * 1024
 # dram__bytes_write.sum of one ncu capture of an 8-step launch after the L2 flush,
 # profiles/step_kernel_mixed_dp45_4M.md).  It holds only for that launch size and for the kernel
 # code it was taken on, identified by kernel_code_hash(); otherwise the benchmark reports null.
-STEP_TRAFFIC = {"bytes_per_launch": 50859008 + 180522752, "steps_per_launch": 8,
-                "code_sha256": "e8fbc2ceb25cbf8a5b2ac2f415531fc49c3b56b5f1a32bf38e6539d8002ee05c"}
+STEP_TRAFFIC = {"bytes_per_launch": 58030080 + 188227328, "steps_per_launch": 8,
+                "code_sha256": "0a0f354d64ef7d9f02c8f6532a9966e052c35839e959e5e414775a9c9ba38ff5"}
 KERNEL_SOURCES = ["step_kernel.cuh", "xflat_internal.cuh", "kernels_2f.cu"]
 
 
