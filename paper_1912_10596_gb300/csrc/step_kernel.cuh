@@ -388,7 +388,8 @@ struct Phys3 {
 // du_j / n_phi and phi_p = 2 pi (p + 1/2) / n_phi.  Besides D and J1 the potential needs
 //   Jc = sum_b w_b (sin th_b / cos th_b) cos phi_b s_b,   Js = the same with sin phi_b,
 // and K = [eta omega B + lambda z + mu (D + (1 - cos th) J1 - sin th (cos phi Jc + sin phi Js))] / cos th.
-// Table row (KT = 10): t1, q, q Bx, q Bz, G0 (3), (sin th / cos th) cos phi, (sin th / cos th) sin phi.
+// Table row: t1, q, q Bx, q Bz, G0 (3), (sin th / cos th) cos phi, (sin th / cos th) sin phi (FP64:
+// KT = 10; FP32: each value twice, KT = 18, so FP32 passes run beam pairs as for the bulb model).
 template <typename Real>
 struct Phys2E {
   static constexpr bool kF32 = sizeof(Real) == 4;
