@@ -43,3 +43,23 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "beam-updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_kernel_code_hash_ignores_comments_only(tmp_path):
+    """The key of the recorded counters changes with the kernel code, not with its comments."""
+    import shutil
+    csrc = tmp_path / "paper_1912_10596_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(ROOT, "paper_1912_10596_gb300", "csrc", f), csrc / f)
+    saved = bench.ROOT
+    try:
+        bench.ROOT = str(tmp_path)
+        h0 = bench.kernel_code_hash()
+        k = csrc / "kernels_2f.cu"
+        k.write_text(k.read_text() + "\n// a comment\n/* and a block\n   comment */\n")
+        assert bench.kernel_code_hash() == h0
+        k.write_text(k.read_text() + "\nstatic int xflat_unused_symbol = 0;\n")
+        assert bench.kernel_code_hash() != h0
+    finally:
+        bench.ROOT = saved
