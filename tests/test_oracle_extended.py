@@ -4,7 +4,8 @@
   model gives the bulb model's result, direction by direction.
 * Rotating the initial state by one azimuthal bin rotates the result by one bin (the potential
   depends on phi - phi' only): a sign or index slip in the sin/cos terms breaks it.
-* A state with a cos(phi) flavour modulation has Phi_sc by hand and Phi_ss = 0.
+* A state with a cos(phi) (sin(phi)) flavour modulation has Phi_sc (Phi_ss) by hand and the other
+  azimuthal moment zero.
 """
 import numpy as np
 import pytest
@@ -68,3 +69,22 @@ def test_cos_phi_modulation_moments():
     want = eps * (w * s).sum() * d * eb.n_phi / 2 * X
     assert np.abs(Phisc - want).max() < 1e-12 * np.abs(want).max()
     assert np.abs(Phiss).max() < 1e-12 * np.abs(want).max()
+
+
+def test_sin_phi_modulation_moments():
+    """A sin(phi) flavour modulation: Phi_ss by hand and Phi_sc = 0 (the mirror of the cos(phi)
+    case; a swapped cos/sin weight or a sign slip in the sin phi' term fails one of the two)."""
+    wl, eb, _ = _case(n_phi=8)
+    eps = 0.02
+    X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    Y = eb.initial_state() + eps * np.sin(eb.phi)[None, None, :, None, None, None] * X
+    r = 45.0
+    Phi1, Phic, Phisc, Phiss = eb.moments(r, eb.flux_matrices(Y[0], Y[1]))
+    g = eb.grid
+    c = eb.cos_theta(r)
+    s = np.sqrt(1 - c * c)
+    w = g.du * wl.R_km**2 / (2 * r * r * c) / eb.n_phi
+    d = (g.N[0, 0] - g.N[0, 1]).sum() - (g.N[1, 0] - g.N[1, 1]).sum()
+    want = eps * (w * s).sum() * d * eb.n_phi / 2 * X          # sum_p sin^2 phi_p = n_phi / 2
+    assert np.abs(Phiss - want).max() < 1e-12 * np.abs(want).max()
+    assert np.abs(Phisc).max() < 1e-12 * np.abs(want).max()

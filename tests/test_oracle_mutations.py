@@ -169,6 +169,7 @@ EXT_PINS = {
     "axial_symmetry": ext_pins.test_axial_symmetry_reduces_to_bulb,
     "shift_symmetry": ext_pins.test_azimuthal_shift_symmetry,
     "cos_phi_moment": ext_pins.test_cos_phi_modulation_moments,
+    "sin_phi_moment": ext_pins.test_sin_phi_modulation_moments,
 }
 
 
@@ -210,7 +211,7 @@ def sine_term_sign(mp):
 
 EXT_CASES = [
     (azimuthal_measure_without_bins, ["axial_symmetry"]),
-    (cos_moment_with_sine_weight, ["cos_phi_moment"]),
+    (cos_moment_with_sine_weight, ["cos_phi_moment", "sin_phi_moment"]),
     (sine_term_sign, ["shift_symmetry"]),
 ]
 
