@@ -3,6 +3,7 @@ CPU, by patching one of its functions for the duration of the case) and checks t
 named beside it fail.  The mistakes are the kind a transcription of the paper's equations makes:
 a flipped sign, a dropped factor, a missing term, a wrong coefficient.
 """
+import math
 import warnings
 
 import numpy as np
@@ -36,6 +37,8 @@ PINS = {
     "order_rk4": lambda: pins.test_convergence_order("rk4", 4),
     "order_dp5": lambda: pins.test_convergence_order("dp5", 5),
     "controller": pins.test_adaptive_controller_meets_tolerance,
+    "vacuum_3f": pins.test_three_flavour_vacuum_closed_form,
+    "power_law": pins.test_power_law_density_profile,
 }
 
 
@@ -133,6 +136,32 @@ def dormand_prince_weight(mp):
     mp.setattr(ig, "DP_B", b)
 
 
+def pmns_reversed_product(mp):
+    """Mixing matrix U = R12 R13 R23 instead of R23 R13 R12."""
+    def pmns(t12, t13, t23):
+        c12, s12, c13, s13 = math.cos(t12), math.sin(t12), math.cos(t13), math.sin(t13)
+        c23, s23 = math.cos(t23), math.sin(t23)
+        R12 = np.array([[c12, s12, 0], [-s12, c12, 0], [0, 0, 1]])
+        R13 = np.array([[c13, 0, s13], [0, 1, 0], [-s13, 0, c13]])
+        R23 = np.array([[1, 0, 0], [0, c23, s23], [0, -s23, c23]])
+        return R12 @ R13 @ R23
+    mp.setattr(ph, "pmns", pmns)
+
+
+def mass_splittings_swapped(mp):
+    """dm2_21 attached to the third mass state and dm2_31 to the second."""
+    def vac(E, n, dm2, theta):
+        return _vac(E, n, (dm2[1], dm2[0]) if n == 3 else dm2, theta)
+    mp.setattr(ph, "vacuum_hamiltonian", vac)
+
+
+def power_law_inverted(mp):
+    """rho0 (r / r_ref)^power instead of rho0 (r_ref / r)^power."""
+    def n_e(r, wl):
+        return wl.Ye * wl.rho0_gcc * (r / wl.r_ref_km) ** wl.power / ph.M_U_G * ph.CM3_PER_KM3
+    mp.setattr(ph, "electron_density_km3", n_e)
+
+
 CASES = [
     (vacuum_sign, ["msw_normal", "msw_inverted", "synchronised"]),
     (no_path_factor, ["vacuum_rk4", "antineutrino", "lepton_number"]),
@@ -146,6 +175,9 @@ CASES = [
     (cos_theta_unsquared, ["vacuum_rk4", "single_angle", "three_to_two", "trace_purity"]),
     (rk4_equal_weights, ["vacuum_rk4", "library_rk", "order_rk4", "trace_purity"]),
     (dormand_prince_weight, ["vacuum_dp45", "order_dp5", "controller"]),
+    (pmns_reversed_product, ["vacuum_3f"]),
+    (mass_splittings_swapped, ["vacuum_3f"]),
+    (power_law_inverted, ["power_law"]),
 ]
 
 

@@ -120,6 +120,53 @@ def test_vacuum_closed_form(method):
     assert abs(exact / 1e3 / float(golden("osc_phase_coeff")) - 1) < 1e-3
 
 
+def test_three_flavour_vacuum_closed_form():
+    """mu = lambda = 0, three flavours with every mixing angle and both mass splittings non-zero:
+    each beam's nu_e survival and nu_e -> nu_mu appearance follow the textbook vacuum formulas
+      P_ee = 1 - 4 sum_{i<j} U_ei^2 U_ej^2 sin^2(dm2_ji L / 4E),
+      P_emu = -4 sum_{i<j} U_ei U_mui U_ej U_muj sin^2(dm2_ji L / 4E)      (real U, delta_CP = 0)
+    along the beam's path length L, with the e and mu rows of the mixing matrix written out from
+    the standard parametrisation (PDG neutrino-mixing review): U_e = (c12 c13, s12 c13, s13),
+    U_mu = (-s12 c23 - c12 s23 s13, c12 c23 - s12 s23 s13, s23 c13).  Pins the product order of
+    the mixing matrix and which vacuum matrix carries which mass splitting."""
+    th, dm = (0.59, 0.15, 0.785), (7.5e-5, 2.4e-3)
+    wl = Workload(name="vac3", n_flavor=3, n_energy=6, n_angle=4, E_min=2.0, E_max=20.0, L=NO_L,
+                  dm2=dm, theta=th)
+    b = Bulb(wl)
+    Y, _ = evolve_fixed(b, b.initial_state(), 11.0, 211.0, 2000, "lie_rk4")
+    c12, s12 = math.cos(th[0]), math.sin(th[0])
+    c13, s13 = math.cos(th[1]), math.sin(th[1])
+    c23, s23 = math.cos(th[2]), math.sin(th[2])
+    Ue = [c12 * c13, s12 * c13, s13]
+    Um = [-s12 * c23 - c12 * s23 * s13, c12 * c23 - s12 * s23 * s13, s23 * c13]
+    m2 = [0.0, dm[0], dm[1]]
+    g = b.grid
+    L = 211.0 * cos_theta(g.u, 11.0, 211.0) - 11.0 * np.sqrt(1.0 - g.u)
+    k = 1.0 / (4 * ph.HBARC_EV_KM * 1e6)             # dm2 L / (4 E): eV^2, km, MeV
+    Pee, Pem = np.ones((4, 6)), np.zeros((4, 6))
+    for i in range(3):
+        for j in range(i + 1, 3):
+            s2 = np.sin(k * (m2[j] - m2[i]) * L[:, None] / g.E[None, :]) ** 2
+            Pee -= 4 * Ue[i] ** 2 * Ue[j] ** 2 * s2
+            Pem -= 4 * Ue[i] * Um[i] * Ue[j] * Um[j] * s2
+    assert Pee.min() < 0.5 and Pem.max() > 0.3        # strong three-flavour oscillation
+    for s in range(2):                                 # antineutrinos: the same in vacuum (delta = 0)
+        assert np.abs(Y[s, ..., 0, 0].real - Pee).max() < 1e-7
+        assert np.abs(Y[s, ..., 1, 1].real - Pem).max() < 1e-7
+
+
+def test_power_law_density_profile():
+    """rho(r) = rho0 (r_ref / r)^power: at r_ref sqrt(2) G_F n_e is the textbook 7.63e-14 eV x Ye x
+    rho0 (converted to 1/km with hbar c), and it falls by 2^power when r doubles."""
+    for power in (3.0, 2.0):
+        wl = Workload(name="pl", matter="power_law", rho0_gcc=1e7, r_ref_km=100.0, power=power, Ye=0.5)
+        lam = ph.matter_strength(100.0, wl)
+        want = float(golden("V_CC_eV_per_Ye_rho")) * 0.5 * 1e7 / ph.HBARC_EV_KM
+        assert abs(lam / want - 1) < 2e-3
+        assert abs(ph.matter_strength(200.0, wl) * 2.0**power / lam - 1) < 1e-14
+        assert abs(ph.matter_strength(50.0, wl) / (lam * 2.0**power) - 1) < 1e-14
+
+
 @pytest.mark.parametrize("sign", [+1.0, -1.0])
 def test_constant_matter_closed_form(sign):
     """Constant lambda, mu = 0: MSW in uniform matter.  Neutrinos see +lambda, antineutrinos
