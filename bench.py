@@ -32,8 +32,7 @@ BYTES_PER_BEAM_STAGE = {("mixed", "dp45"): 14.0, ("fp64", "dp45"): 28.0,
                         ("mixed", "rk4"): 15.0, ("fp64", "rk4"): 30.0}
 L2_BYTES = 129 * 1024 * 1024
 # DRAM traffic of one timed launch of the step kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture of an 8-step launch after the L2 flush,
-# profiles/step_kernel_mixed_dp45_4M.md).  It holds only for that launch size and for the kernel
+# dram__bytes_write.sum of one ncu capture of an 8-step launch after the L2 flush).  It holds only for that launch size and for the kernel
 # code it was taken on, identified by kernel_code_hash(); otherwise the benchmark reports null.
 STEP_TRAFFIC = {"bytes_per_launch": 58030080 + 188227328, "steps_per_launch": 8,
                 "code_sha256": "0a0f354d64ef7d9f02c8f6532a9966e052c35839e959e5e414775a9c9ba38ff5"}

@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
 import subprocess
 import sys
@@ -10,6 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxflat.so")
+STAMP = LIB + ".sha256"      # fingerprint of the inputs the present libxflat.so was built from
 SOURCES = ["api.cu", "kernels_2f.cu", "kernels_2e.cu", "kernels_3f.cu", "adjoint_2f.cu", "noalloc.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-diag-suppress", "128",
@@ -38,18 +40,33 @@ def sources() -> list[str]:
     return [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _fingerprint() -> str:
+    """SHA-256 over every file of csrc/, the public header, this script and the nvcc flags: the
+    library is rebuilt whenever any of them differs from what the present binary was built from
+    (file times are not trusted: a copied tree can carry a binary newer than its sources)."""
+    h = hashlib.sha256()
+    deps = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC))
+    deps += [os.path.join(HERE, "..", "include", "xflat.h"), os.path.abspath(__file__)]
+    for d in deps:
+        if os.path.isfile(d):
+            h.update(os.path.basename(d).encode() + b"\0")
+            with open(d, "rb") as f:
+                h.update(f.read())
+    h.update("\0".join(NVCC_FLAGS + SOURCES).encode())
+    return h.hexdigest()
+
+
+def _stale(fp: str) -> bool:
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
-        os.path.join(HERE, "..", "include", "xflat.h"), __file__]
-    return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
+    with open(STAMP) as f:
+        return f.read().strip() != fp
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile every CUDA translation unit for sm_103a and link libxflat.so in the package."""
-    if not force and not _stale():
+    fp = _fingerprint()
+    if not force and not _stale(fp):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
@@ -66,6 +83,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(fp + "\n")
     return LIB
 
 

@@ -111,7 +111,11 @@ extern "C" int xflat_moments_2f_noalloc(const double* d_state, uint32_t n_energy
   // the completion counter must start at zero (the rows are fully overwritten by every call)
   if (cudaMemsetAsync(scratch, 0, sizeof(double), stream) != cudaSuccess) return XFLAT_ERR_CUDA;
   const double x = (R_km * R_km) / (r_km * r_km);
-  k_moments_rows<<<2 * n_angle, 256, 0, stream>>>(d_state, n_energy, n_angle, d_g, d_u, d_du, x,
-                                                  scratch, d_J);
-  return cudaGetLastError() == cudaSuccess ? XFLAT_OK : XFLAT_ERR_CUDA;
+  // cudaLaunchKernel returns this launch's own error: an unrelated error left pending on the thread
+  // by earlier work is neither reported as this call's failure nor cleared
+  void* args[] = {(void*)&d_state, (void*)&n_energy, (void*)&n_angle, (void*)&d_g, (void*)&d_u,
+                  (void*)&d_du, (void*)&x, (void*)&scratch, (void*)&d_J};
+  const cudaError_t e = cudaLaunchKernel((const void*)k_moments_rows, dim3(2 * n_angle), dim3(256),
+                                         args, 0, stream);
+  return e == cudaSuccess ? XFLAT_OK : XFLAT_ERR_CUDA;
 }
