@@ -34,8 +34,8 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM traffic of one timed launch of the step kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of an 8-step launch after the L2 flush).  It holds only for that launch size and for the kernel
 # code it was taken on, identified by kernel_code_hash(); otherwise the benchmark reports null.
-STEP_TRAFFIC = {"bytes_per_launch": 58030080 + 188227328, "steps_per_launch": 8,
-                "code_sha256": "0a0f354d64ef7d9f02c8f6532a9966e052c35839e959e5e414775a9c9ba38ff5"}
+STEP_TRAFFIC = {"bytes_per_launch": 59444224 + 199951616, "steps_per_launch": 8,
+                "code_sha256": "12ba3306538362de292a151f0be95486a3e796f98e133c3837cd1afe327a9d9a"}
 KERNEL_SOURCES = ["step_kernel.cuh", "xflat_internal.cuh", "kernels_2f.cu"]
 
 
@@ -516,7 +516,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "beams": wl.n_beams, "integrator": "dp45",
-                       "precision": "mixed: f32 per-beam algebra, f64 moment reductions and step control",
+                       "precision": "mixed: f32 per-beam algebra and moment contributions, FP64-accurate (exact integer) moment sums, exact max error norm, f64 step control",
                        "r_start_km": 11.0, "stage_evals_per_step": bsu / wl.n_beams,
                        "steps_per_launch": spl,
                        "l2": f"flushed before every timed launch of up to {spl} steps (write of a 258 MB buffer)",

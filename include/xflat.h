@@ -56,9 +56,13 @@ enum xflat_status {
 /* ---- configuration enums --------------------------------------------------------------------- */
 enum xflat_precision {
   XFLAT_FP64 = 0,             /* every per-beam operation in IEEE double                         */
-  XFLAT_MIXED = 1             /* per-beam precession in float; moment reduction across threads,
-                                 warps, blocks and the grid, the error-norm maximum and the
-                                 step-size controller in double; |s| renormalised every step    */
+  XFLAT_MIXED = 1             /* per-beam precession in float, including each beam's moment
+                                 contribution w s; the sum of the contributions over beams is
+                                 FP64-accurate (per-thread TwoSum pairs, then integer sums across
+                                 threads, warps, blocks and the grid: exact and order-free); the
+                                 error norm is the exact maximum of the per-beam error ratios with
+                                 its square root and the step-size controller in double; |s|
+                                 renormalised every step                                          */
 };
 enum xflat_integrator {
   XFLAT_RK4 = 0,              /* classical 4-stage RK on d(rho)/dr = -i[H,rho]/cos(theta), fixed step */

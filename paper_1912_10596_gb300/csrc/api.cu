@@ -389,8 +389,28 @@ int upload_tables(xflat_t h, uint32_t i) {
   if (h->real_size == 8) {
     CUDA_TRY(h, cudaMemcpy((double*)h->d_etab + I.e_off, et.data(), n * 8, cudaMemcpyHostToDevice));
   } else {
+    // Mixed kernels hand each thread's FP32 moment partial sums to integers in units of 2^-S (see
+    // the step kernel): the weights are uploaded times 2^S, with S the largest integer for which
+    // 2 B 2^S <= 2^52, B = sum_b |w_b| / cos(theta_b)(R) bounding every partial sum of states with
+    // |Y| <= 2 (|t1|, |q| and the extended model's |tan theta| are at most 1/cos theta, largest at
+    // r = R).  The kernel accepts thread and block partials below 2^52 units, so no integer sum
+    // can overflow; the resolution 2^-S of the normalised moments is 2^-50 or finer for B <= 2.
+    const uint32_t ne = I.cfg.n_energy, na = (uint32_t)I.u.size();
+    const int wrow = I.cfg.n_flavor == 2 ? 1 : 2;     // first of the two weight rows (nu, nubar)
+    double B = 0.0;
+    for (uint32_t a = 0; a < na; ++a) {
+      double gs = 0.0;
+      for (int sp = 0; sp < 2; ++sp)
+        for (uint32_t k = 0; k < ne; ++k) gs += std::fabs(et[(size_t)(wrow + sp) * ne + k]);
+      B += std::fabs(I.du[a]) * gs / std::sqrt(1.0 - I.u[a]);
+    }
+    const int S = B > 0 ? std::min(100, 51 - (int)std::ceil(std::log2(B))) : 50;
+    h->ic[i].acc_unit = std::ldexp(1.0, -S);
     std::vector<float> ef(n);
-    for (size_t t = 0; t < n; ++t) ef[t] = (float)et[t];
+    for (size_t t = 0; t < n; ++t) {
+      const bool weight = t >= (size_t)wrow * ne && t < (size_t)(wrow + 2) * ne;
+      ef[t] = (float)(weight ? std::ldexp(et[t], S) : et[t]);
+    }
     CUDA_TRY(h, cudaMemcpy((float*)h->d_etab + I.e_off, ef.data(), n * 4, cudaMemcpyHostToDevice));
   }
   CUDA_TRY(h, cudaMemcpy(h->d_u + I.a_off, I.u.data(), I.u.size() * 8, cudaMemcpyHostToDevice));
@@ -821,6 +841,7 @@ int create_impl(const xflat_config* cfgs, uint32_t n, xflat_t* out) {
     fill_inst_const(h->inst[i], h->ic[i]);
     h->ic[i].wscale = 1.0;
     h->ic[i].mu_coef = 0.0;
+    h->ic[i].acc_unit = std::ldexp(1.0, -50);
     reset_dyn(h, i, h->inst[i].cfg.R_km);
   }
   int rc = setup_launch_shape(h, cfgs[0]);

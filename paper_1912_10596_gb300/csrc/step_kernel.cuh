@@ -23,16 +23,18 @@
 // J0 - cos(th_b) J1 = D + (1 - cos(th_b)) J1, with 1 - cos = u x / (1 + cos), x = R^2/r^2, and
 // 1/cos - 1 = (1 - cos)/cos: every term is computed without cancellation.
 //
-// Reduction.  Each thread accumulates its beams' contributions in the working precision.  FP64
-// path: each block reduces them with a fixed shuffle/shared-memory tree in double and adds its
-// partial to the instance accumulator as a 128-bit fixed-point integer (exact to 2^-64).  Mixed
-// path: each warp reduces with a fixed FP32 shuffle tree and its lane 0 adds the warp's partial as a
-// fixed-point integer with 48 fractional bits, converted from the float's bits on the integer pipe
-// (GB300's FP64 pipe is ~1/68 of its FP32 rate, so a double tree per block would cost more than the
-// beams themselves).  Integer addition is associative, so either grid-level sum is identical
-// whatever order the blocks arrive in.  The last block to arrive at the barrier converts the
-// accumulators, derives the stage constants mu(r_s) D, mu(r_s) J1, lambda(r_s) and runs the
-// step-size controller in double.
+// Reduction.  FP64 path: each thread accumulates its beams' contributions in double, each block
+// reduces them with a fixed shuffle/shared-memory tree in double and adds its partial to the
+// instance accumulator as a 128-bit fixed-point integer (exact to 2^-64).  Mixed path: each beam's
+// contribution is formed in FP32 (per-beam algebra) and summed per thread without rounding loss as
+// an unevaluated (hi, lo) pair (TwoSum); at the end of the pass the pair goes to integers in units
+// of the instance's 2^-S (the FP32 weights carry that power-of-two scale), and the warp shuffle
+// trees, the sum over warps and the grid sum are integer additions.  So the moments are the
+// FP64-accurate sums of the FP32 contributions, with no FP64 instruction per beam (GB300's FP64
+// pipe is ~1/68 of its FP32 rate).  Integer addition is associative, so either grid-level sum is
+// identical whatever order the blocks arrive in.  Every block derives a stage's constants
+// mu(r_s) D, mu(r_s) J1, lambda(r_s) from the integer sums; the last block to arrive at a step's
+// final barrier runs the step-size controller in double.
 #pragma once
 
 #include "xflat_internal.cuh"
@@ -153,6 +155,58 @@ __device__ __forceinline__ void geometry_f(double u, double x, float& q, float& 
 }
 
 // --------------------------------------------------------------------------------------------
+// Per-thread moment accumulators.  FP64 kernels add each beam's contribution w s by FMA into a
+// double.  Mixed kernels form each contribution w s in FP32 (per-beam algebra) and sum the
+// contributions without rounding loss: a component's running sum is the unevaluated pair hi + lo,
+// and TwoSum (Knuth, TAOCP vol. 2, 4.2.2) splits hi + c into the rounded sum and its exact
+// rounding error, which lo collects (lo's own roundings stay near 2^-48 of the sum, as in a
+// double accumulator).  At the end of a pass each thread's pair goes exactly to integers
+// (f32_to_fix) and every further sum is an integer addition.  The FP32 weights carry a
+// per-instance power-of-two scale (InstConst::acc_unit = 2^-S) so that the integers are in units
+// of 2^-S; no FP64 instruction is issued per beam (GB300's FP64 pipe is ~1/68 of its FP32 rate).
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float c) {
+  const float s = __fadd_rn(hi, c);
+  const float bv = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(c, bv));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+template <typename Real, int NM> struct MomAcc;
+template <int NM> struct MomAcc<double, NM> {
+  double v[NM];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) v[i] = 0.0;
+  }
+  __device__ __forceinline__ void add(int i, double w, double y) { v[i] = fma(w, y, v[i]); }
+};
+template <int NM> struct MomAcc<float, NM> {
+  float hi[NM], lo[NM];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NM; ++i) { hi[i] = 0.0f; lo[i] = 0.0f; }
+  }
+  __device__ __forceinline__ void add(int i, float w, float y) { two_sum_acc(hi[i], lo[i], __fmul_rn(w, y)); }
+};
+
+// A float that holds a count of 2^-S units (possibly with a fraction) as the nearest int64 (halves
+// away from zero), from its bits on the integer pipe, branch-free (no FP64 instruction).  Sets ovf
+// when |v| >= 2^52 or v is not finite: a partial that large voids the scale's guarantee.
+__device__ __forceinline__ long long f32_to_fix(float v, int& ovf) {
+  const unsigned int b = __float_as_uint(v);
+  const unsigned int ef = (b >> 23) & 0xffu;
+  ovf |= ef >= 127u + 52u ? 1 : 0;
+  const unsigned int m = ef ? ((b & 0x7fffffu) | 0x800000u) : 0u;   // below 2^-126: zero
+  const int e = (int)ef - 150;                                       // |v| = m 2^e
+  const int rs = min(max(-e, 0), 31);
+  const unsigned int mr = rs ? ((m + (1u << (rs - 1))) >> rs) : m;
+  const unsigned long long r = (unsigned long long)mr << min(max(e, 0), 63);
+  return (b >> 31) ? -(long long)r : (long long)r;
+}
+constexpr long long kFixLimit = 1ll << 52;               // largest block partial accepted
+
+// --------------------------------------------------------------------------------------------
 // Physics policies.  "Real" is the working precision of the per-beam algebra.
 //
 // Two flavours: the state of a beam is the Bloch vector s of P = (1 + s.sigma)/2 (antineutrinos:
@@ -227,12 +281,14 @@ struct Phys2 {
     k[2] = Kv[0] * y[1] - Kv[1] * y[0];
   }
   // moments D (weight w t1) and J1 (weight w)
-  __device__ static inline void accum(Real (&acc)[NM], Real w, Real t1, const Real (&y)[3]) {
+  template <class Acc>
+  __device__ static inline void accum(Acc& acc, Real w, Real t1, const Real (&y)[3]) {
     const Real wt = w * t1;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { acc[i] += wt * y[i]; acc[3 + i] += w * y[i]; }
+    for (int i = 0; i < 3; ++i) { acc.add(i, wt, y[i]); acc.add(3 + i, w, y[i]); }
   }
-  __device__ static inline void accum_row(Real (&acc)[NM], Real w, const Real* row, const Real (&y)[3]) {
+  template <class Acc>
+  __device__ static inline void accum_row(Acc& acc, Real w, const Real* row, const Real (&y)[3]) {
     accum(acc, w, t1(row), y);
   }
   // table row of (stage with constants sc / scf and R^2/r^2 = x, angle bin at u)
@@ -341,10 +397,11 @@ struct Phys3 {
     z[7] = ai[1][2] + ai[2][1];
     z[8] = ar[2][1] - ar[1][2];
   }
-  __device__ static inline void accum(Real (&acc)[NM], Real w, Real t1, const Real (&y)[9]) {
+  template <class Acc>
+  __device__ static inline void accum(Acc& acc, Real w, Real t1, const Real (&y)[9]) {
     const Real wt = w * t1;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) { acc[i] += wt * y[i]; acc[9 + i] += w * y[i]; }
+    for (int i = 0; i < 9; ++i) { acc.add(i, wt, y[i]); acc.add(9 + i, w, y[i]); }
   }
   // ||P - tr(P)/3||_F^2 with off-diagonal entries counted twice
   __device__ static inline Real tnorm2(const Real (&y)[9]) {
@@ -369,7 +426,8 @@ struct Phys3 {
     return m * sqrt(d + 2 * o);
   }
   __device__ static inline void normalise(Real (&)[9]) {}
-  __device__ static inline void accum_row(Real (&acc)[NM], Real w, const Real* row, const Real (&y)[NC]) {
+  template <class Acc>
+  __device__ static inline void accum_row(Acc& acc, Real w, const Real* row, const Real (&y)[NC]) {
     accum(acc, w, t1(row), y);
   }
   __device__ static inline void fill_row(Real* row, double u, double x, const double* sc, const Real* scr,
@@ -457,14 +515,15 @@ struct Phys2E {
   __device__ static inline void f(const Real (&Kv)[3], const Real (&y)[3], Real (&k)[3]) {
     Phys2<Real>::f(Kv, y, k);
   }
-  __device__ static inline void accum_row(Real (&acc)[NM], Real w, const Real* t, const Real (&y)[3]) {
+  template <class Acc>
+  __device__ static inline void accum_row(Acc& acc, Real w, const Real* t, const Real (&y)[3]) {
     const Real wt = w * val(t, vT1), wc = w * val(t, vSCC), ws = w * val(t, vSCS);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      acc[i] += wt * y[i];
-      acc[3 + i] += w * y[i];
-      acc[6 + i] += wc * y[i];
-      acc[9 + i] += ws * y[i];
+      acc.add(i, wt, y[i]);
+      acc.add(3 + i, w, y[i]);
+      acc.add(6 + i, wc, y[i]);
+      acc.add(9 + i, ws, y[i]);
     }
   }
   __device__ static inline Real tnorm2(const Real (&y)[3]) { return Phys2<Real>::tnorm2(y); }
@@ -528,28 +587,6 @@ __device__ __forceinline__ double fx_read(const unsigned long long* acc2) {
   return (double)hi + (double)acc2[0] * 5.421010862427522e-20;   // 2^-64 (words already loaded)
 }
 
-// Mixed precision: a float as a signed fixed-point integer with 48 fractional bits, from its bits
-// alone (integer pipe only; |v| < 2^14 required, truncated toward zero below 2^-48).  Returns
-// false when |v| is too large or not finite.
-__device__ __forceinline__ bool f32_to_fix48(float v, long long& out) {
-  const unsigned int b = __float_as_uint(v);
-  const int e = (int)((b >> 23) & 0xffu);
-  if (e == 0xff || e >= 127 + 14) return false;
-  if (e == 0) { out = 0; return true; }                  // zero or below 2^-126
-  const long long m = (long long)((b & 0x7fffffu) | 0x800000u);   // value = m 2^(e-150)
-  const int sh = e - 102;                                // x 2^48
-  long long f = sh >= 0 ? (m << sh) : (sh > -25 ? (m >> (-sh)) : 0ll);
-  out = (b >> 31) ? -f : f;
-  return true;
-}
-
-// Accumulator read-out: 128-bit (FP64 path) or 48-bit-fraction (mixed path) fixed point.
-template <typename Real>
-__device__ __forceinline__ double acc_read(const unsigned long long* acc2) {
-  if constexpr (sizeof(Real) == 4) return (double)(long long)acc2[0] * 3.552713678800501e-15;  // 2^-48
-  else return fx_read(acc2);
-}
-
 template <class Tab>
 __device__ __forceinline__ double stage_c(int i) { return Tab::c(i); }
 
@@ -601,12 +638,12 @@ __device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
 // Component c of a stage's moments: the kAccCopies fixed-point copies summed as integers (exact,
 // so every block that reads them gets the same bits), then converted to double.
 template <typename Real>
-__device__ __forceinline__ double acc_component(const unsigned long long* acc_slot, int c) {
+__device__ __forceinline__ double acc_component(const unsigned long long* acc_slot, int c, double unit) {
   if constexpr (sizeof(Real) == 4) {
     long long sum = 0;
 #pragma unroll
     for (int cp = 0; cp < kAccCopies; ++cp) sum += (long long)__ldcg(acc_slot + ((size_t)cp * kNMMax + c) * 2);
-    return (double)sum * 3.552713678800501e-15;                  // 2^-48
+    return (double)sum * unit;                                   // 2^-S of the instance
   } else {
     unsigned __int128 sum = 0;
 #pragma unroll
@@ -649,7 +686,7 @@ __device__ int serial_update(const KParams& p, int slot, bool final_pass, bool i
     double m[NM];
     if (have_moments) {
 #pragma unroll
-      for (int c = 0; c < NM; ++c) m[c] = acc_component<Real>(acc, c);
+      for (int c = 0; c < NM; ++c) m[c] = acc_component<Real>(acc, c, ic.acc_unit);
     }
     double m7[NM], sc7[Phys::NSC];
     if (adaptive_final) {
@@ -953,11 +990,11 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
   // final pass gets y5 in y and that ep back.  kst: this beam's element of the stage-derivative
   // planes (component i of k_l at kst[((l - 1) NC + i) kstride]), read and written by this thread
   // only.
-  template <class BS>
+  template <class BS, class Acc>
   __device__ static inline void beam(const BS& bs, const typename Phys::Beam& bm,
                                      const TabView<Real, Phys>& tv, int tj, Real (&y)[NC],
                                      Real (&ep)[NC + 1],
-                                     Real (&acc)[Phys::NM], Real& emax, int& bad, bool mixed,
+                                     Acc& acc, Real& emax, int& bad, bool mixed,
                                      Real* kst, size_t kstride) {
     Real k[Tab::S + 1][NC];
 #pragma unroll
@@ -1108,11 +1145,11 @@ template <class Phys, class Tab, typename Real, int kPass, int kKind>
 struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
   static constexpr int NC = 3;
   static constexpr bool kStore = false;
-  template <class BS>
+  template <class BS, class Acc>
   __device__ static inline void beam(const BS& bs, const typename Phys::Beam& bm,
                                      const TabView<Real, Phys>& tv, int tj, Real (&y)[NC],
                                      Real (&)[NC + 1],
-                                     Real (&acc)[Phys::NM], Real& emax, int& bad, bool mixed,
+                                     Acc& acc, Real& emax, int& bad, bool mixed,
                                      Real*, size_t) {
     if (kKind == kInitPass) {
       Phys::accum_row(acc, bm.w, tv.row(1, tj), y);
@@ -1221,6 +1258,37 @@ __device__ __forceinline__ F2 mul2(F2 a, F2 b) {
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
+__device__ __forceinline__ F2 add2(F2 a, F2 b) {
+  F2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) {
+  F2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// two_sum_acc on a pair (each half one beam): hi + c split into the rounded sum and its exact
+// rounding error, collected in lo.
+__device__ __forceinline__ void two_sum_acc2(F2& hi, F2& lo, F2 c) {
+  const F2 s = add2(hi, c);
+  const F2 bv = sub2(s, hi);
+  const F2 err = add2(sub2(hi, sub2(s, bv)), sub2(c, bv));
+  hi = s;
+  lo = add2(lo, err);
+}
+// Moment accumulators of a thread's beam pairs: component i is the unevaluated sum hi[i] + lo[i].
+template <int NM>
+struct PairAcc {
+  F2 hi[NM], lo[NM];
+};
+// A single (unpaired) beam of a pair kernel accumulates into the first half of the pair
+// accumulators, so those kernels keep one set of accumulator registers.
+template <int NM>
+struct PairHalfAcc {
+  PairAcc<NM>& a;
+  __device__ __forceinline__ void add(int i, float w, float y) { two_sum_acc2(a.hi[i], a.lo[i], pk(__fmul_rn(w, y), 0.0f)); }
+};
 
 template <class P, class Tab, int kPass, int kKind>
 struct PairRK {
@@ -1249,14 +1317,21 @@ struct PairRK {
   }
   // moments of the pair's states with the weights of row R: D (w t1), J1 (w) and, extended model,
   // Jc (w (sin th / cos th) cos phi), Js (w (sin th / cos th) sin phi)
-  __device__ static inline void accum(F2 (&acc)[NM], F2 w, const F2* R, const F2 (&y)[3]) {
+  // (contributions formed in FP32, summed without loss: see MomAcc<float>)
+  __device__ static inline void accum(PairAcc<NM>& acc, F2 w, const F2* R, const F2 (&y)[3]) {
     const F2 wt = mul2(w, R[P::vT1]);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { acc[i] = fma2(wt, y[i], acc[i]); acc[3 + i] = fma2(w, y[i], acc[3 + i]); }
+    for (int i = 0; i < 3; ++i) {
+      two_sum_acc2(acc.hi[i], acc.lo[i], mul2(wt, y[i]));
+      two_sum_acc2(acc.hi[3 + i], acc.lo[3 + i], mul2(w, y[i]));
+    }
     if constexpr (NM == 12) {
       const F2 wc = mul2(w, R[P::vSCC]), ws = mul2(w, R[P::vSCS]);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) { acc[6 + i] = fma2(wc, y[i], acc[6 + i]); acc[9 + i] = fma2(ws, y[i], acc[9 + i]); }
+      for (int i = 0; i < 3; ++i) {
+        two_sum_acc2(acc.hi[6 + i], acc.lo[6 + i], mul2(wc, y[i]));
+        two_sum_acc2(acc.hi[9 + i], acc.lo[9 + i], mul2(ws, y[i]));
+      }
     }
   }
   // 1/sqrt(n2) of a pair: hardware reciprocal square root refined by one Newton step
@@ -1281,7 +1356,7 @@ struct PairRK {
   // y, ep as in PassBody::beam
   template <class BS>
   __device__ static inline void run(const BS& bs, F2 eo, F2 w, const F2* rows, int rstride, F2 (&y)[3],
-                                    F2 (&ep)[4], F2 (&acc)[NM], float& emax, int& bad) {
+                                    F2 (&ep)[4], PairAcc<NM>& acc, float& emax, int& bad) {
     F2 k[Tab::S + 1][3];
     // adaptive final pass: y5 and the error accumulate as soon as each stage derivative exists
     // (same order of operations as summing after the chain), so the derivatives die early
@@ -1372,8 +1447,8 @@ struct PairRK {
       const float atol = bs.atol, rtol = bs.rtol;
       const float s0 = atol + rtol * sqrtf(0.5f * fmaxf(a0, m20));
       const float s1 = atol + rtol * sqrtf(0.5f * fmaxf(a1, m21));
-      float r0 = __fdividef(0.5f * e20, s0 * s0);
-      float r1 = __fdividef(0.5f * e21, s1 * s1);
+      float r0 = __fdiv_rn(0.5f * e20, s0 * s0);
+      float r1 = __fdiv_rn(0.5f * e21, s1 * s1);
       if (!(r0 <= 3.0e38f) || !ok0) r0 = INFINITY;
       if (!(r1 <= 3.0e38f) || !ok1) r1 = INFINITY;
       emax = fmaxf(emax, fmaxf(r0, r1));
@@ -1479,7 +1554,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
                                          (size_t)kNewest * kAccCopies * kNMMax * 2;
         InstDyn* dw = p.dyn + pc.inst;
         if (c < Phys::NM) {
-          const double m = acc_component<Real>(accs, c);
+          const double m = acc_component<Real>(accs, c, ic.acc_unit);
           v = ldcg(&d->mus[kNewest]) * m;
           if (pc.start == 0) dw->mom[kNewest][c] = m;
         } else if (c == Phys::NM) {
@@ -1512,7 +1587,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
                                          (size_t)s * kAccCopies * kNMMax * 2;
         InstDyn* dw = p.dyn + pc.inst;
         if (c < Phys::NM) {
-          const double m = acc_component<Real>(accs, c);
+          const double m = acc_component<Real>(accs, c, ic.acc_unit);
           v = ldcg(&d->mus[s]) * m;
           if (pc.start == 0) dw->mom[s][c] = m;
         } else if (c == Phys::NM) {
@@ -1599,16 +1674,15 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     Real* kst = Body::kStore ? reinterpret_cast<Real*>(p.kst) + ic.beam_off : nullptr;
     const Real* ysrc = kSplitLoad ? yout : yin;
     const int ne = (int)ic.n_energy, na = (int)ic.n_angle;
-    Real acc[NM];
-#pragma unroll
-    for (int i = 0; i < NM; ++i) acc[i] = 0;
+    MomAcc<Real, NM> acc;
+    acc.zero();
     Real emax = 0;
     int bad = 0;
     // FP32 two-flavour RK passes run beam pairs on packed f32x2 arithmetic (PairRK)
     constexpr bool kPair = Phys::kPairable && !kCF;
-    F2 acc2[NM];
+    PairAcc<NM> acc2;
 #pragma unroll
-    for (int i = 0; i < NM; ++i) acc2[i] = 0ull;
+    for (int i = 0; i < NM; ++i) { acc2.hi[i] = 0ull; acc2.lo[i] = 0ull; }
     float emax2 = 0.0f;
     const uint32_t end = pc.start + pc.len;
     const uint32_t vstep = VN * blockDim.x;
@@ -1685,8 +1759,13 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
 #pragma unroll
               for (int c = 0; c <= NC; ++c) ev[c] = ep[c][v];
             }
-            Body::beam(bs, bm, tv, tj, y, ev, acc, emax, bad, mixed, Body::kStore ? kst + l0 + v : nullptr,
-                       p.plane_stride);
+            if constexpr (kPair) {
+              PairHalfAcc<NM> hacc{acc2};
+              Body::beam(bs, bm, tv, tj, y, ev, hacc, emax, bad, mixed, nullptr, p.plane_stride);
+            } else {
+              Body::beam(bs, bm, tv, tj, y, ev, acc, emax, bad, mixed, Body::kStore ? kst + l0 + v : nullptr,
+                         p.plane_stride);
+            }
 #pragma unroll
             for (int c = 0; c < NC; ++c) ys[c][v] = y[c];
             if constexpr (kSplitStore) {
@@ -1708,15 +1787,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
         for (int c = 0; c <= NC; ++c) vstore(escr + (size_t)c * p.plane_stride + l0, ep[c]);
       }
     }
-    if constexpr (kPair) {
-#pragma unroll
-      for (int i = 0; i < NM; ++i) {
-        float a, b;
-        upk(acc2[i], a, b);
-        acc[i] += a + b;
-      }
-      emax = fmax(emax, (Real)emax2);
-    }
+    if constexpr (kPair) emax = fmax(emax, (Real)emax2);
     // the pass forming Y_S also checked the step's input state (non-finite: fatal)
     if constexpr (kSplitStore) {
       const int any_bad = __syncthreads_or(bad);
@@ -1729,9 +1800,12 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     constexpr bool kMoments = kKind != kFinalPass || Tab::kFinalMoments;
     constexpr bool kRejectOverflow = Tab::kAdaptive;
     if constexpr (sizeof(Real) == 4) {
-      // mixed precision: warp trees in FP32, the warps' partials summed in a fixed order, and the
-      // block's partial added to one of the instance's accumulator copies as a fixed-point integer
-      // (integer atomics: order-independent; no FP64 instruction)
+      // mixed precision: each thread's (hi, lo) partial sums go to integers of the instance's
+      // acc_unit; the warp shuffle trees, the sum over warps and the accumulator atomics are
+      // integer additions (exact, order-free).  A thread or block partial of 2^52 units or more
+      // (only a runaway or non-finite state reaches it) rejects an adaptive trial step and is
+      // fatal for a fixed step.  The error maximum is a max (exact); the square root of the
+      // block's maximum is taken in double.
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
       float* redf = reinterpret_cast<float*>(red);
       if constexpr (kErrMax) {
@@ -1750,23 +1824,38 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       }
       if constexpr (kMoments) {
         if constexpr (kErrMax) __syncthreads();              // the scratch is reused
+        long long* redl = reinterpret_cast<long long*>(red);  // [warp][NM]
+        int ovf = 0;
 #pragma unroll
-        for (int i = 0; i < NM; ++i)
+        for (int i = 0; i < NM; ++i) {
+          // the thread's partial (pair halves and scalar accumulator joined by TwoSum), then a warp
+          // shuffle tree on the (hi, lo) pairs, each step a TwoSum with the error added to lo
+          // (lo's FP32 additions round near 2^-48 of the partial), and lane 0 turns the warp's
+          // pair into integers of 2^-S units
+          float hi, lo;
+          if constexpr (kPair) {
+            float b, lb;
+            upk(acc2.hi[i], hi, b);
+            upk(acc2.lo[i], lo, lb);
+            two_sum_acc(hi, lo, b);
+            lo = __fadd_rn(lo, lb);
+          } else {
+            hi = acc.hi[i];
+            lo = acc.lo[i];
+          }
+          long long v = f32_to_fix(hi, ovf) + f32_to_fix(lo, ovf);
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
-        if (lane == 0) {
-#pragma unroll
-          for (int i = 0; i < NM; ++i) redf[warp * NM + i] = (float)acc[i];
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+          if (lane == 0) redl[warp * NM + i] = v;
         }
-        __syncthreads();
+        const int any_ovf = __syncthreads_or(ovf);
         if (threadIdx.x < NM) {
-          float sum = 0.0f;
-          for (int w = 0; w < nw; ++w) sum += redf[w * NM + threadIdx.x];
-          long long fx;
+          long long v = 0;
+          for (int w = 0; w < nw; ++w) v += redl[w * NM + threadIdx.x];
           unsigned long long* a = p.acc + (size_t)pc.inst * kAccWordsPerInst +
                                   (((size_t)slot * kAccCopies + blockIdx.x % kAccCopies) * kNMMax + threadIdx.x) * 2;
-          if (f32_to_fix48(sum, fx)) {
-            atomicAdd(a, (unsigned long long)fx);
+          if (!any_ovf && v < kFixLimit && v > -kFixLimit) {
+            atomicAdd(a, (unsigned long long)v);
           } else if (kRejectOverflow) {
             atomicMax(&p.errmax[pc.inst], 0x7ff0000000000000ull);   // overflowing trial step
           } else {
@@ -1788,7 +1877,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       if constexpr (kMoments) {
         double v[NM];
 #pragma unroll
-        for (int i = 0; i < NM; ++i) v[i] = (double)acc[i];
+        for (int i = 0; i < NM; ++i) v[i] = acc.v[i];
         block_sum<NM>(v, red);
         if (threadIdx.x == 0) {
           bool fin = true;

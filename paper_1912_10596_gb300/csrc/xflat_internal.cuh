@@ -41,6 +41,7 @@ struct InstConst {
   double R2;                // R^2 (km^2)
   double mu_coef;           // mu(r) = mu_coef / r^2, includes the weight scale wscale
   double wscale;            // physical per-bin number luminosity of a unit table weight (1/s)
+  double acc_unit;          // mixed kernels: value of one unit of the fixed-point moment sums (2^-S)
   double lam_coef, power, lam_const, r_ref;   // lambda(r) = lam_coef (r_ref / r)^power
   int32_t matter;
   int32_t adaptive;

@@ -52,8 +52,10 @@ def test_large_2f_mixed_full_size(xf):
     Yr = s.get_rho().reshape(Y0.shape)
     J0, J1 = s.moments()
     R0, R1 = b.moment_matrices(wl.r0, Yr)
-    assert np.abs(J0 - R0).max() <= 3e-6 * np.abs(R0).max()         # FP32 products and warp sums
-    assert np.abs(J1 - R1).max() <= 3e-6 * np.abs(R1).max()
+    # the sums are FP64-accurate (pinned exactly in test_mixed_reduction_gpu); what remains is the
+    # FP32 rounding of the weights, here systematic: du = 1/2000 is not a float (3.8e-8 relative)
+    assert np.abs(J0 - R0).max() <= 1e-7 * np.abs(R0).max()
+    assert np.abs(J1 - R1).max() <= 1e-7 * np.abs(R1).max()
     assert abs(R1[0, 1]) > 0.1 * abs(R1[0, 0] - R1[1, 1])          # coherent: large off-diagonal
     s.advance([wl.r1], max_steps=1)
     st = s.stats()
