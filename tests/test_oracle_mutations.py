@@ -39,6 +39,8 @@ PINS = {
     "controller": pins.test_adaptive_controller_meets_tolerance,
     "vacuum_3f": pins.test_three_flavour_vacuum_closed_form,
     "power_law": pins.test_power_law_density_profile,
+    "lie_richardson": pins.test_lie_richardson_estimate_is_the_local_error,
+    "lie_tolerance": pins.test_lie_adaptive_meets_tolerance,
 }
 
 
@@ -162,6 +164,22 @@ def power_law_inverted(mp):
     mp.setattr(ph, "electron_density_km3", n_e)
 
 
+def richardson_divisor(mp):
+    """Richardson estimate divided by 2^5 - 1 (the order of the local error) instead of 2^4 - 1."""
+    mp.setattr(ig, "RICHARDSON_DIV", 31.0)
+
+
+def second_half_step_from_start(mp):
+    """The second half step taken from the step's initial state instead of the first half step's."""
+    def step(G, r, Y, h, G1=None):
+        if G1 is None:
+            G1 = G(r, Y)
+        full = ig.cf4_step(G, r, Y, h, G1)
+        ig.cf4_step(G, r, Y, 0.5 * h, G1)
+        return ig.cf4_step(G, r + 0.5 * h, Y, 0.5 * h), full
+    mp.setattr(ig, "lie_richardson_step", step)
+
+
 CASES = [
     (vacuum_sign, ["msw_normal", "msw_inverted", "synchronised"]),
     (no_path_factor, ["vacuum_rk4", "antineutrino", "lepton_number"]),
@@ -178,6 +196,8 @@ CASES = [
     (pmns_reversed_product, ["vacuum_3f"]),
     (mass_splittings_swapped, ["vacuum_3f"]),
     (power_law_inverted, ["power_law"]),
+    (richardson_divisor, ["lie_richardson"]),
+    (second_half_step_from_start, ["lie_tolerance"]),
 ]
 
 
