@@ -34,8 +34,8 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM traffic of one timed launch of the step kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of an 8-step launch after the L2 flush).  It holds only for that launch size and for the kernel
 # code it was taken on, identified by kernel_code_hash(); otherwise the benchmark reports null.
-STEP_TRAFFIC = {"bytes_per_launch": 59444224 + 199951616, "steps_per_launch": 8,
-                "code_sha256": "12ba3306538362de292a151f0be95486a3e796f98e133c3837cd1afe327a9d9a"}
+STEP_TRAFFIC = {"bytes_per_launch": 64039936 + 208817664, "steps_per_launch": 8,
+                "code_sha256": "5ba7bcd51c720eafaa0f85ca850c0640c3c826ef7bc41038af58db9c9cf40b4f"}
 KERNEL_SOURCES = ["step_kernel.cuh", "xflat_internal.cuh", "kernels_2f.cu"]
 
 
@@ -165,7 +165,41 @@ def time_device_steps(xf, torch, wl, precision, steps, warmup, flush, shape=None
     if st1.status != 0:
         raise RuntimeError(f"device status {st1.status}")
     bsu = (st1.beam_stage_updates - st0.beam_stage_updates) / steps
+    acc = st1.accepted - st0.accepted
+    s.timed_accepted_fraction = acc / max(1, acc + st1.rejected - st0.rejected)
     return ms, chunks, bsu, st1, s
+
+
+def time_more_steps(torch, s, steps, flush, per_launch):
+    """Time `steps` further radial steps of an existing solver (launches of up to per_launch steps,
+    the L2 flushed before each).  Returns (ms per step, beam-stage updates per step, accepted
+    steps, attempted steps)."""
+    stream = torch.cuda.current_stream()
+    st0 = s.stats()
+    chunks = launch_chunks(steps, per_launch)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in chunks]
+    for (e0, e1), n in zip(evs, chunks):
+        flush(); e0.record(stream)
+        s.advance(None, max_steps=n)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    st1 = s.stats()
+    if st1.status != 0:
+        raise RuntimeError(f"device status {st1.status}")
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    acc = st1.accepted - st0.accepted
+    att = acc + st1.rejected - st0.rejected
+    return ms / steps, (st1.beam_stage_updates - st0.beam_stage_updates) / steps, acc, att
+
+
+def repeat_stats(torch, s, steps, repeats, flush, per_launch):
+    """Median, minimum and maximum of `repeats` timings of `steps` steps each."""
+    runs = [time_more_steps(torch, s, steps, flush, per_launch) for _ in range(repeats)]
+    ms = [r[0] for r in runs]
+    return {"repeats": repeats, "steps_per_repeat": steps, "ms_per_step_median": statistics.median(ms),
+            "ms_per_step_min": min(ms), "ms_per_step_max": max(ms),
+            "beam_stage_updates_per_step": runs[0][1],
+            "accepted_fraction": sum(r[2] for r in runs) / max(1, sum(r[3] for r in runs))}
 
 
 def e2e_steps(xf, torch, s, wl, steps):
@@ -215,6 +249,95 @@ def cpu_baseline(seconds=12.0, impl_steps=None):
     dt = time.perf_counter() - t0
     beams = 2 * 20 * wl.n_energy
     return beams * 6 * n / dt, n, dt, beams
+
+
+def _cpu_worker(seconds):
+    v, n, dt, beams = cpu_baseline(seconds)
+    return v, n
+
+
+def cpu_baseline_all_cores(seconds=12.0):
+    """The same bounded oracle sample run as independent copies on every host core at once (the
+    oracle's beams are coupled through the moments at every stage, so one sample does not split
+    across processes): the summed rate of the copies, with the process count."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(n) as pool:
+        res = pool.map(_cpu_worker, [seconds] * n)
+    return sum(v for v, _ in res), n, sum(k for _, k in res)
+
+
+def matched_error(xf, torch, log=None):
+    """Mixed and batched forms against the plain FP64 path at matched survival-probability error.
+
+    Each candidate integrates the same window from the initial condition; its error is the largest
+    |P_ee - P_ee,ref| over every beam against the FP64 DP45 run at rtol = atol = 1e-9 (the GPU FP64
+    path, itself pinned to the oracle at 1e-10).  The speedup at 1e-4 is the time of the fastest
+    FP64 candidate whose error is within 1e-4 over that of the fastest mixed candidate within 1e-4.
+    Windows (no matter, so that the collective flavour evolution of the small case's physics
+    happens inside them): the 4M-beam grid over 100 -> 110 km; the 64 batched instances over
+    100 -> 101 km, the mixed form all instances in one persistent launch per chunk of steps, the
+    FP64 path one instance after another."""
+    from bulb_inputs import Workload, batched_workloads
+    stream = torch.cuda.current_stream()
+
+    def run(wls, precision, integrator, tol, r0, r1, per_instance):
+        groups = [[w] for w in wls] if per_instance else [wls]
+        ms, acc, rej, pees = 0.0, 0, 0, []
+        for grp in groups:
+            cfgs = [xf.config_from_workload(w, precision=precision, integrator=integrator, rtol=tol,
+                                            atol=tol, h0_km=1e-3, steps_per_launch=64) for w in grp]
+            for c in cfgs:
+                c.cuda_stream = stream.cuda_stream
+            sv = xf.Solver(cfgs)
+            for i, w in enumerate(grp):
+                sv.set_spectra(w.spectra(), inst=i)
+            sv.reset(r0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if len(grp) == 1:
+                sv.evolve(r0, r1)
+            else:
+                sv.evolve_batch([r1] * len(grp))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            for i in range(len(grp)):
+                st = sv.stats(inst=i)
+                acc, rej = acc + st.accepted, rej + st.rejected
+                pees.append(sv.pee(inst=i)[0])
+            sv.close()
+        return ms, acc, rej, np.concatenate(pees)
+
+    def compare(name, wls, r0, r1, batched):
+        ref_ms, ra, rr, ref = run(wls, "fp64", "dp45", 1e-9, r0, r1, True)
+        rows = [{"form": "fp64 dp45 rtol 1e-9 (reference)", "precision": "fp64", "ms": ref_ms,
+                 "accepted": ra, "rejected": rr, "max_abs_dpee": 0.0}]
+        plan = [("fp64", "dp45", 1e-6, True), ("fp64", "lie_adaptive", 1e-6, True),
+                ("mixed", "dp45", 1e-6, not batched), ("mixed", "lie_adaptive", 1e-6, not batched)]
+        for prec, integ, tol, per in plan:
+            ms, a, r, pee = run(wls, prec, integ, tol, r0, r1, per)
+            rows.append({"form": f"{prec} {integ} rtol {tol:g}" + (" (all instances in one launch)" if not per else ""),
+                         "precision": prec, "ms": ms, "accepted": a, "rejected": r,
+                         "max_abs_dpee": float(np.abs(pee - ref).max())})
+            if log:
+                log(json.dumps(rows[-1]))
+        ok64 = [x["ms"] for x in rows if x["precision"] == "fp64" and x["max_abs_dpee"] <= 1e-4]
+        okmx = [x["ms"] for x in rows if x["precision"] == "mixed" and x["max_abs_dpee"] <= 1e-4]
+        return {"window_km": [r0, r1], "beams": int(sum(w.n_beams for w in wls)), "instances": len(wls),
+                "pee_change": float(np.abs(ref - 1.0).max()), "runs": rows,
+                "speedup_at_1e-4": (min(ok64) / min(okmx)) if ok64 and okmx else None}
+
+    big = workload_2f_large("mixed")
+    big.matter = "none"
+    single = compare("4M", [big], 100.0, 110.0, False)
+    batch = [w for w in batched_workloads()]
+    for w in batch:
+        w.matter = "none"
+    batched = compare("batched", batch, 100.0, 101.0, True)
+    return single, batched
 
 
 def compare_integrators():
@@ -382,6 +505,52 @@ def measure_configs(only=None):
         line(wl.name, nb, bsu, ms, 16, 14.0, window="16 DP45 steps from 11 km",
              block_size=sv.stats().block_size, blocks=sv.stats().grid_blocks)
         sv.close()
+    # the configured radial ranges from r = R: the 4M-beam case with the adaptive exact propagators
+    # (mixed at rtol 1e-6 over all of 11 -> 500 km; FP64 at 1e-6 and 1e-9 for a bounded wall time),
+    # and the explicit DP45 step near R for comparison (mixed 4M beams; FP64 three flavours, the
+    # exponential schemes being two-flavour only)
+    if want("range"):
+        from bulb_inputs import workload_2f_large
+        budget = 30.0
+
+        def range_run(wl, precision, integrator, tol, r1, n_per_launch=64):
+            cfg = xf.config_from_workload(wl, precision=precision, integrator=integrator, rtol=tol, atol=tol,
+                                          h0_km=1e-9, steps_per_launch=n_per_launch)
+            sv = solver([cfg], [wl.spectra()])
+            sv.reset(wl.r0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            sv.advance([r1], max_steps=n_per_launch)
+            marks = []
+            while True:
+                sv.advance(None, max_steps=n_per_launch)
+                torch.cuda.synchronize()
+                st = sv.stats()
+                marks.append((round(time.perf_counter() - t0, 3), st.r_km, int(st.accepted), int(st.rejected)))
+                if st.r_km >= r1 or st.status or time.perf_counter() - t0 > budget:
+                    break
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = sv.stats()
+            pee, mean = sv.pee()
+            out = {"workload": wl.name, "integrator": integrator, "precision": precision, "rtol": tol,
+                   "beams": wl.n_beams, "r_start_km": wl.r0, "r_reached_km": st.r_km, "r_target_km": r1,
+                   "accepted": int(st.accepted), "rejected": int(st.rejected), "status": int(st.status),
+                   "device_ms": e0.elapsed_time(e1), "wall_s": time.perf_counter() - t0,
+                   "beam_stage_updates": int(st.beam_stage_updates), "pee_min": float(pee.min()),
+                   "pee_mean": float(mean), "progress": marks[:: max(1, len(marks) // 10)]}
+            print(json.dumps(out), flush=True)
+            sv.close()
+
+        big = workload_2f_large("mixed")
+        range_run(big, "mixed", "lie_adaptive", 1e-6, big.r1)
+        range_run(big, "fp64", "lie_adaptive", 1e-6, big.r1)
+        range_run(big, "fp64", "lie_adaptive", 1e-9, big.r1)
+        range_run(big, "mixed", "dp45", 1e-6, big.r1, n_per_launch=256)
+        wl3 = workload_3f_fp64()
+        range_run(wl3, "fp64", "dp45", 1e-9, wl3.r1, n_per_launch=256)
     if not want("adjoint"):
         return
 
@@ -412,13 +581,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--no-matched", action="store_true",
+                    help="skip the speedups at matched survival-probability error")
+    ap.add_argument("--repeats", type=int, default=5, help="repeats behind the median timings")
     ap.add_argument("--steps-per-launch", type=int, default=8,
                     help="radial steps per persistent launch in the timed region (L2 flushed before each)")
     ap.add_argument("--compare-integrators", action="store_true",
                     help="accuracy against cost of the integrators on the 4096-beam case instead of the benchmark")
     ap.add_argument("--configs", action="store_true",
                     help="device rates of the other workloads (small, three-flavour, batched, adjoint) instead of the benchmark")
-    ap.add_argument("--only", choices=["small", "3f", "batched", "extended", "adjoint"],
+    ap.add_argument("--only", choices=["small", "3f", "batched", "extended", "adjoint", "range"],
                     help="with --configs: measure one of the workloads")
     args = ap.parse_args()
     if args.compare_integrators:
@@ -482,6 +654,7 @@ def main():
     with ClockSampler(torch.cuda.current_device()) as clk:
         ms, chunks, bsu, st, solver = time_device_steps(xf, torch, wl, "mixed", args.steps, args.warmup,
                                                         flush, shape, spl)
+        rep_main = repeat_stats(torch, solver, max(200, args.steps), args.repeats, flush, spl)
     clocks = clk.summary()
     t_ms = shard.max_over_ranks(sum(ms))                      # the slowest rank's time
     value = world * bsu * args.steps / (t_ms / 1e3)
@@ -490,25 +663,42 @@ def main():
     # bytes over the mean launch duration when the launches are equal)
     achieved = BYTES_PER_BEAM_STAGE[("mixed", "dp45")] * bsu * args.steps / (sum(ms) / 1e3) / 1e9
 
+    # accepted-only rate: the stages of accepted steps only (a rejected DP45 attempt evaluates 6
+    # stages too); the all-attempt rate is `value`
+    acc_frac = solver.timed_accepted_fraction
     fp64 = None
     if not args.no_fp64:
-        k64 = max(3, args.steps // 4)
+        k64 = max(20, args.steps // 4)
         ms64, _, bsu64, st64, s64 = time_device_steps(xf, torch, wl, "fp64", k64, args.warmup, flush,
                                                       None, spl)
         v64 = bsu64 * k64 / (sum(ms64) / 1e3)
+        rep64 = repeat_stats(torch, s64, k64, args.repeats, flush, spl)
         fp64 = {"value": v64, "unit": "beam-updates/s", "ms_per_step": sum(ms64) / k64,
-                "speedup_mixed_vs_fp64": (bsu * args.steps / (sum(ms) / 1e3)) / v64}
-        del s64
+                "repeats": rep64,
+                "speedup_mixed_vs_fp64_per_step": (bsu * args.steps / (sum(ms) / 1e3)) / v64}
+        s64.close()
     e2e = None
     if not args.no_e2e:
-        v_e2e, bi, bo = e2e_steps(xf, torch, solver, wl, max(3, args.steps // 4))
-        e2e = {"value": world * v_e2e, "unit": "beam-updates/s", "h2d_bytes_per_step": bi,
-               "d2h_bytes_per_step": bo}
+        k_e2e = max(20, args.steps // 4)
+        runs = [e2e_steps(xf, torch, solver, wl, k_e2e) for _ in range(args.repeats)]
+        v_e2e = statistics.median(r[0] for r in runs)
+        e2e = {"value": world * v_e2e, "unit": "beam-updates/s", "h2d_bytes_per_step": runs[0][1],
+               "d2h_bytes_per_step": runs[0][2], "steps_per_repeat": k_e2e, "repeats": args.repeats,
+               "median_of_repeats": True}
+    matched = None
+    if rank == 0 and not args.no_matched:
+        single, batched = matched_error(xf, torch, log=lambda m: print(m, file=sys.stderr))
+        matched = {"speedup_mixed_vs_fp64_at_1e-4": single["speedup_at_1e-4"],
+                   "speedup_batched_vs_fp64_at_1e-4": batched["speedup_at_1e-4"],
+                   "single": single, "batched": batched}
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, n, dt, beams = cpu_baseline()
+        v_all, nproc, n_all = cpu_baseline_all_cores()
         cpu = {"value": v, "unit": "beam-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"FP64 numpy oracle, {n} Dormand-Prince steps at r = 11 km on 1000 E x first 20 of 2000 u bins x (nu, nubar) = {beams} beams, {dt:.1f} s"}
+               "sample": f"FP64 numpy oracle, {n} Dormand-Prince steps at r = 11 km on 1000 E x first 20 of 2000 u bins x (nu, nubar) = {beams} beams, {dt:.1f} s",
+               "all_cores": {"value": v_all, "unit": "beam-updates/s", "cores": nproc, "nproc": nproc,
+                             "sample": f"the same sample as {nproc} independent processes (spawn), 12 s each, {n_all} steps in all"}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "beam-updates/s", "n_gpus": world,
@@ -527,8 +717,13 @@ def main():
                          "note": f"{BYTES_PER_BEAM_STAGE[('mixed', 'dp45')]} algorithmic B per beam-stage "
                                  f"({BYTES_PER_BEAM_STAGE[('mixed', 'dp45')] * bsu * spl / 1e9:.2f} GB per {spl}-step launch); "
                                  f"traffic = DRAM bytes per {spl}-step launch; peak {peak_kind}"},
+            "accepted_value": value * acc_frac,
+            "repeats": rep_main,
             "clocks": clocks,
             "gpu_launches": len(chunks),
+            "matched_error": matched,
+            "speedup_mixed_vs_fp64_at_1e-4": matched["speedup_mixed_vs_fp64_at_1e-4"] if matched else None,
+            "speedup_batched_vs_fp64_at_1e-4": matched["speedup_batched_vs_fp64_at_1e-4"] if matched else None,
             "fp64_path": fp64,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -69,12 +69,21 @@ enum xflat_integrator {
   XFLAT_DP45 = 1,             /* Dormand-Prince 5(4), FSAL, adaptive (error control below)        */
   XFLAT_LIE_RK4 = 2,          /* commutator-free Lie RK4 whose every update is an exact propagator
                                  exp(-i H dl) of Eq. U (two flavours only), fixed step              */
-  XFLAT_EXP_MIDPOINT = 3      /* exponential midpoint rule (Lie-group Runge-Kutta-Munthe-Kaas method
+  XFLAT_EXP_MIDPOINT = 3,     /* exponential midpoint rule (Lie-group Runge-Kutta-Munthe-Kaas method
                                  with Runge's midpoint tableau; Sec. 3.4's exact propagator of Eq. U
                                  with a mid-point scheme): y' = exp(-i H(r+h/2, y_half) dl) applied
                                  to y, y_half from an exponential half step; the exponential Euler
                                  step exp(-i H(r, y) dl) is the embedded first-order estimate
                                  (error control as DP45 with the factor 0.9 Err^-1/2); two flavours */
+  XFLAT_LIE_ADAPTIVE = 4      /* adaptive exact propagators: the commutator-free Lie RK4 of
+                                 XFLAT_LIE_RK4 with Richardson step-size control -- each attempt
+                                 takes one step of h and two of h/2 from the same state, keeps the
+                                 two half steps and estimates their error as (y_two - y_full)/15;
+                                 error norm, acceptance and controller as DP45 (0.9 Err^-1/5).
+                                 Every update is an exact propagator of Eq. U, so the step is set by
+                                 how fast the generator changes, not by its size (no explicit
+                                 stability limit near R).  11 passes (stage evaluations) per step;
+                                 two flavours, bulb model (n_phi <= 1)                               */
 };
 enum xflat_matter {
   XFLAT_MATTER_NONE = 0,

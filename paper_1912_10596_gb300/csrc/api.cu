@@ -112,7 +112,13 @@ bool is_fin(double x) { return std::isfinite(x); }
 // combined angle bins (u x phi) of an instance: n_angle, times n_phi for the extended bulb model
 uint32_t angle_bins(const xflat_config& c) { return c.n_angle * (c.n_phi >= 2 ? c.n_phi : 1u); }
 // integrators with embedded error control (adaptive step size)
-bool adaptive(uint32_t integrator) { return integrator == XFLAT_DP45 || integrator == XFLAT_EXP_MIDPOINT; }
+bool adaptive(uint32_t integrator) {
+  return integrator == XFLAT_DP45 || integrator == XFLAT_EXP_MIDPOINT || integrator == XFLAT_LIE_ADAPTIVE;
+}
+// stage slots (0..S) of the integrator's tableau: the rows of the step kernel's shared-memory table
+int table_stages(int integrator) {
+  return integrator == XFLAT_DP45 ? 8 : integrator == XFLAT_EXP_MIDPOINT ? 4 : integrator == XFLAT_LIE_ADAPTIVE ? 12 : 5;
+}
 
 int check_config(const xflat_config& c, std::string& why) {
   if (c.abi_version != XFLAT_ABI_VERSION) { why = "abi_version mismatch"; return XFLAT_ERR_INVAL; }
@@ -124,9 +130,13 @@ int check_config(const xflat_config& c, std::string& why) {
   if (nb >= (1ull << 31)) { why = "too many beams in one instance"; return XFLAT_ERR_INVAL; }
   if (nb * (uint64_t)c.n_energy >= (1ull << 40)) { why = "n_beams * n_energy must be < 2^40"; return XFLAT_ERR_INVAL; }
   if (c.precision > 1) { why = "precision must be FP64 or MIXED"; return XFLAT_ERR_INVAL; }
-  if (c.integrator > 3) { why = "unknown integrator"; return XFLAT_ERR_INVAL; }
-  if ((c.integrator == XFLAT_LIE_RK4 || c.integrator == XFLAT_EXP_MIDPOINT) && c.n_flavor != 2) {
+  if (c.integrator > 4) { why = "unknown integrator"; return XFLAT_ERR_INVAL; }
+  if ((c.integrator == XFLAT_LIE_RK4 || c.integrator == XFLAT_EXP_MIDPOINT || c.integrator == XFLAT_LIE_ADAPTIVE) &&
+      c.n_flavor != 2) {
     why = "the exponential integrators are two-flavour only"; return XFLAT_ERR_UNSUPPORTED;
+  }
+  if (c.integrator == XFLAT_LIE_ADAPTIVE && c.n_phi >= 2) {
+    why = "the adaptive Lie integrator is built for the bulb model only"; return XFLAT_ERR_UNSUPPORTED;
   }
   if (c.matter_kind > 2) { why = "unknown matter_kind"; return XFLAT_ERR_INVAL; }
   if (!(c.R_km > 0) || !is_fin(c.R_km)) { why = "R_km must be > 0"; return XFLAT_ERR_INVAL; }
@@ -467,7 +477,7 @@ int table_row_values(int nf, size_t real_size, bool ext = false) {
   if (ext) return real_size == 4 ? 18 : 10;
   return nf == 2 ? (real_size == 4 ? 24 : 8) : 4;
 }
-// combined angle rows per piece: bounded by the shared-memory table ([8 stages][rows][row values]);
+// combined angle rows per piece: bounded by the shared-memory table ([stage slots][rows][row values]);
 // the extended model has ten times the rows per beam, so its rows are kept narrow and a block's
 // share of a 4M-beam problem (about 130 rows at two blocks per SM) fits one piece
 uint32_t max_jj_cap(int nf, size_t real_size, bool ext) {
@@ -475,9 +485,9 @@ uint32_t max_jj_cap(int nf, size_t real_size, bool ext) {
   return kMaxJJ;
 }
 
-size_t smem_bytes(int nf, size_t real_size, int max_jj, bool ext = false) {
+size_t smem_bytes(int nf, size_t real_size, int max_jj, int stages, bool ext = false) {
   size_t s = 32 * kNMMax * sizeof(double);
-  s += (size_t)kMaxStages * max_jj * table_row_values(nf, real_size, ext) * real_size;
+  s += (size_t)stages * max_jj * table_row_values(nf, real_size, ext) * real_size;
   s += (size_t)max_jj * real_size;                 // angle weights
   s = (s + 7) / 8 * 8 + (size_t)max_jj * sizeof(double);   // angle positions
   return (s + 15) / 16 * 16;
@@ -648,7 +658,8 @@ int setup_launch_shape(xflat_t h, const xflat_config& c) {
   h->kernel = step_kernel_ptr(h->nf, h->precision, h->integrator, h->block, want_bps * h->block >= 768 ? 3 : 2,
                               h->extended);
   if (!h->kernel) return fail(h, XFLAT_ERR_UNSUPPORTED, "no kernel for this flavour/precision/integrator");
-  const size_t smax = smem_bytes(h->nf, h->real_size, max_jj_cap(h->nf, h->real_size, h->extended), h->extended);
+  const size_t smax = smem_bytes(h->nf, h->real_size, max_jj_cap(h->nf, h->real_size, h->extended),
+                                 table_stages(h->integrator), h->extended);
   CUDA_TRY(h, cudaFuncSetAttribute(h->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
   int occ = 0;
   CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h->kernel, h->block, smax));
@@ -662,7 +673,7 @@ int setup_launch_shape(xflat_t h, const xflat_config& c) {
   G = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)G, (T + per_block - 1) / per_block));
   h->grid = G;
   build_pieces(h, G);
-  h->smem = smem_bytes(h->nf, h->real_size, h->max_jj, h->extended);
+  h->smem = smem_bytes(h->nf, h->real_size, h->max_jj, table_stages(h->integrator), h->extended);
   CUDA_TRY(h, cudaMalloc(&h->d_pieces, sizeof(Piece) * std::max<size_t>(1, h->pieces.size())));
   CUDA_TRY(h, cudaMalloc(&h->d_blk, sizeof(int) * h->blk.size()));
   CUDA_TRY(h, cudaMemcpy(h->d_pieces, h->pieces.data(), sizeof(Piece) * h->pieces.size(), cudaMemcpyHostToDevice));

@@ -8,6 +8,8 @@ struct KParams;
 // up to 256 threads, one block), or nullptr.
 const void* step_kernel_ptr(int n_flavor, int precision, int integrator, int block, int blocks_per_sm,
                             bool extended = false);
+// The adaptive Lie integrator's step kernels (two flavours, bulb model; kernels_lie.cu).
+const void* step_kernel_ptr_lie(int precision, int block, int blocks_per_sm);
 // The extended bulb model's step kernels (two flavours, up to 256 threads, one block per SM).
 const void* step_kernel_ptr_2e(int precision, int integrator, int block);
 }  // namespace xflat

@@ -17,6 +17,7 @@ const void* mixed_2f(int integrator) {
 }
 
 const void* step_kernel_ptr_2f(int precision, int integrator, int block, int blocks_per_sm) {
+  if (integrator == kLieAdaptive) return step_kernel_ptr_lie(precision, block, blocks_per_sm);
   if (block > 256) return (precision == 1 && block == 512) ? mixed_2f<1, 512>(integrator) : nullptr;
   if (precision == 0) {
     if (integrator == kRK4) return (const void*)&step_kernel<Phys2<double>, TabRK4, double, false, 1>;

@@ -48,6 +48,7 @@ namespace xflat {
 // kFinalMoments (the final pass reduces the moments of the new state: stage 1 of the next step),
 // kEvalsPerStep (new stage evaluations per step), kEM2 (exponential midpoint rule).
 struct TabRK4 {
+  static constexpr bool kRichardson = false;
   static constexpr int S = 4;
   static constexpr int kPasses = 4;
   static constexpr bool kAdaptive = false;
@@ -69,6 +70,7 @@ struct TabRK4 {
 
 // Dormand & Prince (1980) 5(4) pair; b = row 7 of A (first same as last), e = b - bhat.
 struct TabDP45 {
+  static constexpr bool kRichardson = false;
   static constexpr int S = 7;
   static constexpr int kPasses = 7;
   static constexpr bool kAdaptive = true;
@@ -102,6 +104,7 @@ struct TabDP45 {
 
 // Commutator-free Lie RK4 (Celledoni, Marthinsen & Owren 2003): stage radii as classical RK4.
 struct TabCF4 {
+  static constexpr bool kRichardson = false;
   static constexpr int S = 4;
   static constexpr int kPasses = 4;
   static constexpr bool kAdaptive = false;
@@ -120,6 +123,7 @@ struct TabCF4 {
 // (generator K1), stage 2 at r + h/2 from the half step Y_half = exp(h/2 K1) y, the new state
 // exp(h K2) y, the estimate exp(h K1) y; stage 3 is the new state at r + h (the next step's stage 1).
 struct TabEM2 {
+  static constexpr bool kRichardson = false;
   static constexpr int S = 3;
   static constexpr int kPasses = 2;
   static constexpr bool kAdaptive = true;
@@ -131,6 +135,32 @@ struct TabEM2 {
   __host__ __device__ static constexpr double b(int) { return 0.0; }
   __host__ __device__ static constexpr double e(int) { return 0.0; }
   __host__ __device__ static constexpr double c(int i) { return i == 1 ? 0.0 : (i == 2 ? 0.5 : 1.0); }
+};
+
+// Commutator-free Lie RK4 (as TabCF4) with Richardson step-size control: every attempt takes the
+// full step of size h and two half steps from the same state, keeps the two half steps and
+// estimates their local error as (y_two - y_full) / (2^4 - 1) (error norm, acceptance and
+// controller as DP45, exponent 1/5).  Stage slots and radii r + c h:
+//   1 (c = 0): y;  full step: 2 (1/2), 3 (1/2), 4 (1);  first half step: 5 (1/4), 6 (1/4), 7 (1/2);
+//   8 (1/2): the first half step's result y_a;  second half step from y_a: 9 (3/4), 10 (3/4), 11 (1).
+// Pass p reduces slot p + 2; the final pass forms y_b (two half steps) and y_full, the error, and
+// the moments of y_b at r + h (the next step's slot 1).
+struct TabCFR {
+  static constexpr bool kRichardson = true;
+  static constexpr int S = 11;
+  static constexpr int kPasses = 11;
+  static constexpr bool kAdaptive = true;
+  static constexpr int kErrPow = 5;
+  static constexpr bool kFinalMoments = true;
+  static constexpr int kEvalsPerStep = 11;
+  static constexpr bool kEM2 = false;
+  __host__ __device__ static constexpr double a(int, int) { return 0.0; }
+  __host__ __device__ static constexpr double b(int) { return 0.0; }
+  __host__ __device__ static constexpr double e(int) { return 0.0; }
+  __host__ __device__ static constexpr double c(int i) {
+    return i == 1 ? 0.0 : (i == 2 || i == 3 || i == 7 || i == 8) ? 0.5 : (i == 5 || i == 6) ? 0.25
+         : (i == 9 || i == 10) ? 0.75 : 1.0;
+  }
 };
 
 // Largest finite value of the working precision.
@@ -1145,6 +1175,137 @@ template <class Phys, class Tab, typename Real, int kPass, int kKind>
 struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
   static constexpr int NC = 3;
   static constexpr bool kStore = false;
+  // rotation of y by d K (the propagator of Eq. U over the path length d for generator K)
+  __device__ static inline void rot(Real (&y)[3], const Real (&K)[3], Real d) {
+    Real Om[3] = {d * K[0], d * K[1], d * K[2]};
+    rotate(Om, y);
+  }
+  // the fourth stage state of a CF4 step of size hh from y with generators Ka (its first stage)
+  // and Kc (its third): exp(hh (Kc - Ka/2)) exp(hh/2 Ka) y
+  __device__ static inline void cf4_stage4(Real (&y)[3], const Real (&Ka)[3], const Real (&Kc)[3], Real hh) {
+    rot(y, Ka, Real(0.5) * hh);
+    const Real D[3] = {Kc[0] - Real(0.5) * Ka[0], Kc[1] - Real(0.5) * Ka[1], Kc[2] - Real(0.5) * Ka[2]};
+    rot(y, D, hh);
+  }
+  // the CF4 update of size hh from y with the step's four generators
+  __device__ static inline void cf4_final(Real (&y)[3], const Real (&K1)[3], const Real (&K2)[3],
+                                          const Real (&K3)[3], const Real (&K4)[3], Real hh) {
+    Real Om[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      Om[i] = hh * (Real(0.25) * K1[i] + Real(1.0 / 6.0) * (K2[i] + K3[i]) - Real(1.0 / 12.0) * K4[i]);
+    rotate(Om, y);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      Om[i] = hh * (Real(-1.0 / 12.0) * K1[i] + Real(1.0 / 6.0) * (K2[i] + K3[i]) + Real(0.25) * K4[i]);
+    rotate(Om, y);
+  }
+  template <class BS>
+  __device__ static inline void gen(const BS& bs, const typename Phys::Beam& bm, const TabView<Real, Phys>& tv,
+                                    int tj, int s, Real (&K)[3]) {
+    Phys::K(tv.row(s, tj), bm, bs.vac, bs.scr[s], K);
+  }
+  // Richardson-controlled CF4 (TabCFR): pass p forms the stage state of slot p + 2 from y; the
+  // final pass forms both results, the error ratio and the moments of the kept result.
+  template <class BS, class Acc>
+  __device__ static inline void richardson(const BS& bs, const typename Phys::Beam& bm,
+                                           const TabView<Real, Phys>& tv, int tj, Real (&y)[3], Acc& acc,
+                                           Real& emax, int& bad, bool mixed) {
+    const Real h = bs.hB[0], hh = Real(0.5) * h;
+    constexpr int I = kKind == kFinalPass ? 0 : kPass + 2;   // slot formed by this pass
+    Real K1[3];
+    gen(bs, bm, tv, tj, 1, K1);
+    if constexpr (I >= 2 && I <= 4) {
+      // full step: Y2 = exp(h/2 K1) y, Y3 = exp(h/2 K2) y, Y4 = exp(h (K3 - K1/2)) exp(h/2 K1) y
+      if constexpr (I == 2) {
+        rot(y, K1, hh);
+      } else if constexpr (I == 3) {
+        Real K2[3];
+        gen(bs, bm, tv, tj, 2, K2);
+        rot(y, K2, hh);
+      } else {
+        Real K3[3];
+        gen(bs, bm, tv, tj, 3, K3);
+        cf4_stage4(y, K1, K3, h);
+      }
+      Phys::accum_row(acc, bm.w, tv.row(I, tj), y);
+      return;
+    }
+    if constexpr (I >= 5 && I <= 7) {
+      // first half step: slots 5, 6, 7 as 2, 3, 4 with hh and generators K1, K5, K6
+      if constexpr (I == 5) {
+        rot(y, K1, Real(0.5) * hh);
+      } else if constexpr (I == 6) {
+        Real K5[3];
+        gen(bs, bm, tv, tj, 5, K5);
+        rot(y, K5, Real(0.5) * hh);
+      } else {
+        Real K6[3];
+        gen(bs, bm, tv, tj, 6, K6);
+        cf4_stage4(y, K1, K6, hh);
+      }
+      Phys::accum_row(acc, bm.w, tv.row(I, tj), y);
+      return;
+    }
+    // everything later starts from the first half step's result y_a (slot 8)
+    Real y0[3] = {y[0], y[1], y[2]};
+    {
+      Real K5[3], K6[3], K7[3];
+      gen(bs, bm, tv, tj, 5, K5);
+      gen(bs, bm, tv, tj, 6, K6);
+      gen(bs, bm, tv, tj, 7, K7);
+      cf4_final(y, K1, K5, K6, K7, hh);
+    }
+    if constexpr (I == 8) {
+      Phys::accum_row(acc, bm.w, tv.row(8, tj), y);
+      return;
+    }
+    Real K8[3];
+    gen(bs, bm, tv, tj, 8, K8);
+    if constexpr (I >= 9 && I <= 11) {
+      if constexpr (I == 9) {
+        rot(y, K8, Real(0.5) * hh);
+      } else if constexpr (I == 10) {
+        Real K9[3];
+        gen(bs, bm, tv, tj, 9, K9);
+        rot(y, K9, Real(0.5) * hh);
+      } else {
+        Real K10[3];
+        gen(bs, bm, tv, tj, 10, K10);
+        cf4_stage4(y, K8, K10, hh);
+      }
+      Phys::accum_row(acc, bm.w, tv.row(I, tj), y);
+      return;
+    } else {
+      // final pass: y_b = the second half step from y_a, y_full = the full step from y0
+      {
+        Real K9[3], K10[3], K11[3];
+        gen(bs, bm, tv, tj, 9, K9);
+        gen(bs, bm, tv, tj, 10, K10);
+        gen(bs, bm, tv, tj, 11, K11);
+        cf4_final(y, K8, K9, K10, K11, hh);
+      }
+      Real yf[3] = {y0[0], y0[1], y0[2]};
+      {
+        Real K2[3], K3[3], K4[3];
+        gen(bs, bm, tv, tj, 2, K2);
+        gen(bs, bm, tv, tj, 3, K3);
+        gen(bs, bm, tv, tj, 4, K4);
+        cf4_final(yf, K1, K2, K3, K4, h);
+      }
+      Real e[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) e[i] = (y[i] - yf[i]) * Real(1.0 / 15.0);
+      if (!(Phys::tnorm2(y0) <= rbig<Real>())) bad = 1;       // non-finite input state: fatal
+      const bool ynok = Phys::tnorm2(y) <= rbig<Real>();
+      const Real den = bs.atol + bs.rtol * sqrt(fmax(Phys::tnorm2(y0), Phys::tnorm2(y)));
+      Real r2 = Phys::tnorm2(e) / (den * den);
+      if (!(r2 <= rbig<Real>()) || !ynok) r2 = Real(INFINITY);
+      emax = fmax(emax, r2);
+      if (mixed && ynok) Phys::normalise(y);
+      Phys::accum_row(acc, bm.w, tv.row(11, tj), y);
+    }
+  }
   template <class BS, class Acc>
   __device__ static inline void beam(const BS& bs, const typename Phys::Beam& bm,
                                      const TabView<Real, Phys>& tv, int tj, Real (&y)[NC],
@@ -1156,6 +1317,10 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
       return;
     }
     const Real h = bs.hB[0];
+    if constexpr (Tab::kRichardson) {
+      richardson(bs, bm, tv, tj, y, acc, emax, bad, mixed);
+      return;
+    }
     if constexpr (Tab::kEM2) {
       // exponential midpoint rule: half step with K1 -> Y_half (moments at r + h/2); final pass:
       // y' = exp(h K2) y, the estimate exp(h K1) y, the error ratio, moments of y' at r + h
@@ -1507,8 +1672,9 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
   constexpr int NC = Phys::NC, NM = Phys::NM, VN = Vec16<Real>::N;
   using Body = PassBody<Phys, Tab, Real, kCF, kPass, kKind>;
   double* red = reinterpret_cast<double*>(dyn_smem);                 // 32 * NM doubles
-  Real* tab = reinterpret_cast<Real*>(red + 32 * kNMMax);            // [kMaxStages][max_jj][KT]
-  Real* dut = tab + (size_t)kMaxStages * p.max_jj * Phys::KT;        // [max_jj]
+  constexpr int kTS = Tab::S + 1;                                    // table stage slots 0..S
+  Real* tab = reinterpret_cast<Real*>(red + 32 * kNMMax);            // [kTS][max_jj][KT]
+  Real* dut = tab + (size_t)kTS * p.max_jj * Phys::KT;               // [max_jj]
   double* ut = reinterpret_cast<double*>(                            // [max_jj], 8-byte aligned
       (reinterpret_cast<uintptr_t>(dut + p.max_jj) + 7) & ~uintptr_t(7));
   const bool mixed = sizeof(Real) == 4;
@@ -1575,7 +1741,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       bs.parity = par;
     }
     const double h = Tab::kAdaptive ? ldcg(&d->h) : ldcg(&d->h_fixed);
-    for (int t = threadIdx.x; t < kMaxStages * Phys::NSC; t += blockDim.x) {
+    for (int t = threadIdx.x; t < kTS * Phys::NSC; t += blockDim.x) {
       const int s = t / Phys::NSC, c = t % Phys::NSC;
       double v = 0.0;
       if (s == kNewest) {
@@ -1653,7 +1819,7 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     }
     // table rows: every needed stage, or (incremental) only the newest and the formed stage
     const unsigned fill = incremental ? (need & (3u << kNewest)) : need;
-    for (int t = threadIdx.x; t < kMaxStages * n_jj; t += blockDim.x) {
+    for (int t = threadIdx.x; t < kTS * n_jj; t += blockDim.x) {
       const int s = t / n_jj, tj = t % n_jj;
       if (!((fill >> s) & 1u)) continue;
       Real* row = tab + ((size_t)s * n_jj + tj) * Phys::KT;

@@ -13,7 +13,7 @@
 
 namespace xflat {
 
-constexpr int kMaxStages = 8;       // DP45: 7 stages; index 0 unused
+constexpr int kMaxStages = 12;      // stage slots 0..11 (Richardson-controlled CF4: 11 stages)
 constexpr int kNM2 = 6;             // 2 flavours: j0 (3) and j1 (3) Bloch components
 constexpr int kNM3 = 18;            // 3 flavours: j0 and j1, 9 reals each
 constexpr int kNSC2 = 8;            // stage constants: mu*j0 (3), mu*j1 (3), lambda, R^2/r^2
@@ -27,7 +27,7 @@ constexpr int kAccCopies = 8;
 // accumulator words per instance: [stage slot][copy][component][2]
 constexpr int kAccWordsPerInst = kMaxStages * kAccCopies * kNMMax * 2;
 
-enum Integrator : int { kRK4 = 0, kDP45 = 1, kLieRK4 = 2, kExpMid = 3 };
+enum Integrator : int { kRK4 = 0, kDP45 = 1, kLieRK4 = 2, kExpMid = 3, kLieAdaptive = 4 };
 enum Matter : int { kMatterNone = 0, kMatterPower = 1, kMatterConst = 2 };
 
 // Instance constants, written by the host before a launch.

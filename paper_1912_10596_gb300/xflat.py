@@ -17,11 +17,12 @@ _lib = C.CDLL(_LIB_PATH)
 ABI_VERSION = 1
 OK, ERR_INVAL, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_STEP, ERR_STATE, ERR_UNSUPPORTED = range(9)
 FP64, MIXED = 0, 1
-RK4, DP45, LIE_RK4, EXP_MIDPOINT = 0, 1, 2, 3
+RK4, DP45, LIE_RK4, EXP_MIDPOINT, LIE_ADAPTIVE = 0, 1, 2, 3, 4
 MATTER_NONE, MATTER_POWER_LAW, MATTER_CONSTANT = 0, 1, 2
 LAYOUT_MATRIX, LAYOUT_NATIVE = 0, 1
 
-_INTEGRATORS = {"rk4": RK4, "dp45": DP45, "lie_rk4": LIE_RK4, "exp_midpoint": EXP_MIDPOINT}
+_INTEGRATORS = {"rk4": RK4, "dp45": DP45, "lie_rk4": LIE_RK4, "exp_midpoint": EXP_MIDPOINT,
+                "lie_adaptive": LIE_ADAPTIVE}
 _MATTER = {"none": MATTER_NONE, "power_law": MATTER_POWER_LAW, "constant": MATTER_CONSTANT}
 _PRECISION = {"fp64": FP64, "mixed": MIXED}
 

@@ -3,7 +3,7 @@ import numpy as np
 
 from bulb_inputs import Workload, random_unit_states
 from oracle.physics import Bulb, Grid
-from oracle.integrate import evolve_fixed, evolve_adaptive, evolve_em2
+from oracle.integrate import evolve_fixed, evolve_adaptive, evolve_em2, evolve_lie_adaptive
 
 
 def beams(Y):
@@ -42,6 +42,9 @@ def oracle_run(wl, Y0, r0, r1, grid=None):
     b = Bulb(wl, grid=grid)
     if wl.integrator == "exp_midpoint":
         Y, r, st = evolve_em2(b, Y0, r0, r1, wl.rtol, wl.atol, wl.h0)
+        return Y, st
+    if wl.integrator == "lie_adaptive":
+        Y, r, st = evolve_lie_adaptive(b, Y0, r0, r1, wl.rtol, wl.atol, wl.h0)
         return Y, st
     if wl.integrator == "dp45":
         Y, r, st = evolve_adaptive(b, Y0, r0, r1, wl.rtol, wl.atol, wl.h0)

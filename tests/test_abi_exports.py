@@ -61,6 +61,12 @@ def test_create_rejects_bad_config_before_touching_the_gpu(lib_path):
     assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_UNSUPPORTED
     c.integrator = xflat.EXP_MIDPOINT
     assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_UNSUPPORTED
+    c.integrator = xflat.LIE_ADAPTIVE
+    assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_UNSUPPORTED
     c = xflat.default_config()
-    c.integrator = 4
+    c.integrator = xflat.LIE_ADAPTIVE
+    c.n_phi = 4
+    assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_UNSUPPORTED
+    c = xflat.default_config()
+    c.integrator = 5
     assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_INVAL
