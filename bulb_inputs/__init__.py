@@ -158,12 +158,14 @@ class Workload:
     L: dict = field(default_factory=lambda: {"nue": 1e51, "nuebar": 1e51, "nux": 1e51, "nuxbar": 1e51})
     meanE: dict = field(default_factory=lambda: {"nue": 11.0, "nuebar": 16.0, "nux": 25.0, "nuxbar": 25.0})
     eta: float = 3.0
-    matter: str = "none"                 # none | power_law | constant
+    matter: str = "none"                 # none | power_law | constant | table
     rho0_gcc: float = 1e7
     r_ref_km: float = 100.0
     power: float = 3.0
     Ye: float = 0.5
     lambda_const: float = 0.0
+    matter_table_r: Optional[list] = None        # matter == "table": radii (km), increasing
+    matter_table_lambda: Optional[list] = None   # and sqrt(2) G_F n_e there (1/km), > 0
     r0: float = 11.0
     r1: float = 200.0
     integrator: str = "rk4"              # rk4 | dp45 | lie_rk4

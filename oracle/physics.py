@@ -88,12 +88,29 @@ def electron_density_km3(r_km: float, wl) -> float:
     return wl.Ye * rho / M_U_G * CM3_PER_KM3
 
 
+def matter_table_strength(r_km: float, r_tab, lam_tab) -> float:
+    """sqrt(2) G_F n_e(r) from a table (r_i, lambda_i), r increasing, lambda > 0: linear in
+    (log r, log lambda) between neighbouring points (each interval a power law, so a table sampled
+    from rho0 (r_ref/r)^p reproduces it exactly), the end values outside the table."""
+    r_tab = np.asarray(r_tab, dtype=np.float64)
+    lam_tab = np.asarray(lam_tab, dtype=np.float64)
+    if r_km <= r_tab[0]:
+        return float(lam_tab[0])
+    if r_km >= r_tab[-1]:
+        return float(lam_tab[-1])
+    i = int(np.searchsorted(r_tab, r_km, side="right")) - 1
+    t = math.log(r_km / r_tab[i]) / math.log(r_tab[i + 1] / r_tab[i])
+    return float(lam_tab[i] * (lam_tab[i + 1] / lam_tab[i]) ** t)
+
+
 def matter_strength(r_km: float, wl) -> float:
     """sqrt(2) G_F n_e(r) in 1/km (the coefficient of diag(1, 0[, 0]) in H_mat, Sec. 2)."""
     if wl.matter == "none":
         return 0.0
     if wl.matter == "constant":
         return float(wl.lambda_const)
+    if wl.matter == "table":
+        return matter_table_strength(r_km, wl.matter_table_r, wl.matter_table_lambda)
     return sqrt2_GF_kmi_per_km3() * electron_density_km3(r_km, wl)
 
 
@@ -137,6 +154,11 @@ class Bulb:
     geometry = "homogeneous": a test geometry with every beam radial (cos theta = 1 in the
     derivative) and an isotropic nu-nu potential H_nunu = mu0 * sum_b F_b / S, where
     S = sum of all per-bin number luminosities; it serves the synchronisation check.
+    geometry = "single_angle": the single-angle approximation of the bulb model: every beam moves
+    along the radial trajectory (cos theta = 1 in the derivative) and the nu-nu potential carries
+    the geometric factor of Eq. Hnu integrated over emission uniform in u = sin^2 theta_R,
+    int_0^1 du (1/sqrt(1 - u x) - 1) = (1 - sqrt(1 - x))^2 / x, x = R^2/r^2, applied to the
+    angle-summed flux: H_nunu = sqrt(2) G_F/(4 pi r^2 c) ((1 - sqrt(1 - x))^2 / x) sum_j du_j F_j.
     """
 
     def __init__(self, wl, grid: Grid | None = None, geometry: str = "bulb", mu0: float = 0.0):
@@ -156,7 +178,7 @@ class Bulb:
 
     # geometry -----------------------------------------------------------------------------------
     def cos_theta(self, r: float) -> np.ndarray:
-        if self.geometry == "homogeneous":
+        if self.geometry in ("homogeneous", "single_angle"):
             return np.ones_like(self.grid.u)
         return cos_theta(self.grid.u, self.wl.R_km, r)
 
@@ -194,6 +216,12 @@ class Bulb:
         if self.geometry == "homogeneous":
             Ftot = np.einsum("j,jkab->ab", self.grid.du, F)
             H = self.mu0 * Ftot / self.S
+            return np.broadcast_to(H, (len(self.grid.u), self.n, self.n))
+        if self.geometry == "single_angle":
+            x = (self.wl.R_km / r) ** 2
+            geo = (1.0 - math.sqrt(1.0 - x)) ** 2 / x
+            Ftot = np.einsum("j,jkab->ab", self.grid.du, F)
+            H = self.K * self.wl.R_km**2 / (2.0 * r * r) * geo * Ftot
             return np.broadcast_to(H, (len(self.grid.u), self.n, self.n))
         Fsum = F.sum(axis=1)                                 # energy integral
         c = self.cos_theta(r)

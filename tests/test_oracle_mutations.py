@@ -41,6 +41,8 @@ PINS = {
     "power_law": pins.test_power_law_density_profile,
     "lie_richardson": pins.test_lie_richardson_estimate_is_the_local_error,
     "lie_tolerance": pins.test_lie_adaptive_meets_tolerance,
+    "single_angle_bulb": pins.test_single_angle_geometry_is_the_bulb_on_the_radial_beam,
+    "matter_table": pins.test_matter_table_reproduces_a_power_law,
 }
 
 
@@ -180,6 +182,25 @@ def second_half_step_from_start(mp):
     mp.setattr(ig, "lie_richardson_step", step)
 
 
+def single_angle_factor_unsquared(mp):
+    """Single-angle geometric factor (1 - sqrt(1 - x)) / x instead of (1 - sqrt(1 - x))^2 / x."""
+    def nff(self, r, F):
+        if self.geometry != "single_angle":
+            return _nff(self, r, F)
+        x = (self.wl.R_km / r) ** 2
+        Ftot = np.einsum("j,jkab->ab", self.grid.du, F)
+        H = self.K * self.wl.R_km**2 / (2.0 * r * r) * (1.0 - math.sqrt(1.0 - x)) / x * Ftot
+        return np.broadcast_to(H, (len(self.grid.u), self.n, self.n))
+    mp.setattr(Bulb, "nunu_from_flux", nff)
+
+
+def matter_table_linear(mp):
+    """Table interpolated linearly in (r, lambda) instead of as a power law per interval."""
+    def tab(r, rt, lt):
+        return float(np.interp(r, rt, lt))
+    mp.setattr(ph, "matter_table_strength", tab)
+
+
 CASES = [
     (vacuum_sign, ["msw_normal", "msw_inverted", "synchronised"]),
     (no_path_factor, ["vacuum_rk4", "antineutrino", "lepton_number"]),
@@ -198,6 +219,8 @@ CASES = [
     (power_law_inverted, ["power_law"]),
     (richardson_divisor, ["lie_richardson"]),
     (second_half_step_from_start, ["lie_tolerance"]),
+    (single_angle_factor_unsquared, ["single_angle_bulb"]),
+    (matter_table_linear, ["matter_table"]),
 ]
 
 

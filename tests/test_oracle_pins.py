@@ -600,3 +600,58 @@ def test_lie_adaptive_steps_far_beyond_the_explicit_limit():
     Yt, _, st8 = evolve_lie_adaptive(b, Y0, 11.0, 11.01, 1e-8, 1e-8, 1e-9, max_attempts=1000)
     assert st8.accepted < 200
     assert np.abs(Y - Yt).max() < 1e-5
+
+
+# --- single-angle geometry and tabulated matter profile ----------------------------------------
+def test_single_angle_geometry_is_the_bulb_on_the_radial_beam():
+    """The single-angle potential equals the multi-angle bulb's potential on a radial probe beam
+    when every beam carries the same state, in the limit of fine u bins (the bulb's midpoint sum
+    over u converges at second order to the integral the single-angle factor closes)."""
+    r = 22.0
+    Y1 = None
+    errs = []
+    for Nu in (16, 32, 64):
+        wl = Workload(name="sa", n_energy=3, n_angle=Nu)
+        u = np.concatenate([(np.arange(Nu) + 0.5) / Nu, [0.0]])
+        du = np.concatenate([np.full(Nu, 1.0 / Nu), [0.0]])
+        b = Bulb(wl, grid=Grid.from_workload(wl, u=u, du=du))
+        sa = Bulb(wl, grid=Grid.from_workload(wl, u=u, du=du), geometry="single_angle")
+        Y = b.initial_state()
+        Y[..., 0, 1] = 0.3
+        Y[..., 1, 0] = 0.3
+        Hb = b.nunu_hamiltonian(r, Y[0], Y[1])[-1]
+        Hs = sa.nunu_hamiltonian(r, Y[0], Y[1])[0]
+        errs.append(abs(Hb[0, 1] - Hs[0, 1]) / abs(Hs[0, 1]))
+    assert errs[-1] < 2e-3
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
+def test_single_angle_bins_evolve_as_one():
+    """Angle bins are indistinguishable in the single-angle geometry: four bins of weight 1/4 evolve
+    exactly as one bin of weight 1, whatever their u."""
+    kw = dict(n_energy=5, matter="constant", lambda_const=0.5)
+    wl4, wl1 = Workload(name="s4", n_angle=4, **kw), Workload(name="s1", n_angle=1, **kw)
+    g4 = Grid.from_workload(wl4, u=np.array([0.1, 0.4, 0.7, 0.95]), du=np.full(4, 0.25))
+    g1 = Grid.from_workload(wl1, u=np.array([0.3]), du=np.array([1.0]))
+    b4, b1 = Bulb(wl4, grid=g4, geometry="single_angle"), Bulb(wl1, grid=g1, geometry="single_angle")
+    Y4, _ = evolve_fixed(b4, b4.initial_state(), 40.0, 42.0, 200, "rk4")
+    Y1, _ = evolve_fixed(b1, b1.initial_state(), 40.0, 42.0, 200, "rk4")
+    assert pee(Y1).min() < 0.9995
+    for j in range(4):
+        assert np.abs(Y4[:, j] - Y1[:, 0]).max() < 1e-13
+
+
+def test_matter_table_reproduces_a_power_law():
+    """A table sampled from rho0 (r_ref/r)^3 gives the power law's lambda between its points (each
+    interval is interpolated as a power law), the end values outside it, and the same evolution."""
+    pl = Workload(name="pl", n_energy=4, n_angle=3, matter="power_law")
+    rt = [10.0, 30.0, 100.0, 300.0, 1000.0]
+    tab = Workload(name="tb", n_energy=4, n_angle=3, matter="table", matter_table_r=rt,
+                   matter_table_lambda=[ph.matter_strength(r, pl) for r in rt])
+    for r in (10.0, 11.0, 47.3, 100.0, 777.0):
+        assert abs(ph.matter_strength(r, tab) / ph.matter_strength(r, pl) - 1) < 1e-13
+    assert ph.matter_strength(5.0, tab) == ph.matter_strength(10.0, pl)
+    assert ph.matter_strength(2000.0, tab) == ph.matter_strength(1000.0, pl)
+    Ya, _ = evolve_fixed(Bulb(pl), Bulb(pl).initial_state(), 300.0, 301.0, 50, "lie_rk4")
+    Yb, _ = evolve_fixed(Bulb(tab), Bulb(tab).initial_state(), 300.0, 301.0, 50, "lie_rk4")
+    assert np.abs(Ya - Yb).max() < 1e-12
