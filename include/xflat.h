@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define XFLAT_ABI_VERSION 1u
+#define XFLAT_ABI_VERSION 2u
 
 /* ---- status codes ---------------------------------------------------------------------------- */
 enum xflat_status {
@@ -88,7 +88,22 @@ enum xflat_integrator {
 enum xflat_matter {
   XFLAT_MATTER_NONE = 0,
   XFLAT_MATTER_POWER_LAW = 1, /* n_e = Ye rho0 (r_ref/r)^power / m_u                               */
-  XFLAT_MATTER_CONSTANT = 2   /* sqrt(2) G_F n_e = lambda_const_kmi at every r                     */
+  XFLAT_MATTER_CONSTANT = 2,  /* sqrt(2) G_F n_e = lambda_const_kmi at every r                     */
+  XFLAT_MATTER_TABLE = 3      /* sqrt(2) G_F n_e from a table (xflat_set_matter_table): a power law
+                                 lambda_i (r/r_i)^p_i on each interval [r_i, r_{i+1}), p_i fixed by
+                                 the two end values (a table sampled from rho0 (r_ref/r)^p gives that
+                                 profile exactly), the end values outside the table              */
+};
+enum xflat_geometry {
+  XFLAT_GEOMETRY_BULB = 0,    /* the bulb model of Sec. 2: cos theta_b(r) = sqrt(1 - u_j R^2/r^2),
+                                 H_nunu = mu(r) (J0 - cos theta_b J1) (Eq. Hnu)                    */
+  XFLAT_GEOMETRY_SINGLE_ANGLE = 1, /* single-angle approximation: every beam moves radially
+                                 (cos theta = 1 in Eq. eom) and H_nunu = mu(r) f(x) J1 with
+                                 f(x) = (1 - sqrt(1 - x))^2 / x, x = R^2/r^2: the geometric factor of
+                                 Eq. Hnu integrated over emission uniform in u                      */
+  XFLAT_GEOMETRY_HOMOGENEOUS = 2 /* test geometry: every beam radial and H_nunu = mu_const_kmi J1 /
+                                 (sum of all per-bin number luminosities), independent of r; the
+                                 synchronised-precession limit of the paper's collective term      */
 };
 enum xflat_layout {
   XFLAT_LAYOUT_MATRIX = 0,    /* [n_beams][n][n] complex double, interleaved (re, im), row major,
@@ -131,7 +146,9 @@ typedef struct {
                                  the L2, 256 otherwise)                                          */
   uint32_t blocks_per_sm;     /* resident blocks per SM for the persistent grid (0 = occupancy)    */
   uint32_t steps_per_launch;  /* radial steps per persistent launch in xflat_evolve (0 = 64)       */
-  uint32_t reserved1;
+  uint32_t geometry;          /* xflat_geometry (0 = the bulb model); SINGLE_ANGLE and HOMOGENEOUS
+                                 need n_phi <= 1                                                    */
+  double mu_const_kmi;        /* XFLAT_GEOMETRY_HOMOGENEOUS: the nu-nu strength mu0 in 1/km       */
 } xflat_config;
 
 typedef struct xflat_s* xflat_t;
@@ -180,6 +197,14 @@ int xflat_destroy(xflat_t h);
 int xflat_set_spectra(xflat_t h, const double* nnu, const double* u_bins, const double* u_weights);
 int xflat_set_spectra_inst(xflat_t h, uint32_t inst, const double* nnu, const double* u_bins,
                            const double* u_weights);
+
+/* Matter profile of instance inst when its matter_kind is XFLAT_MATTER_TABLE (Sec. 2: H_mat with
+ * the electron density n_e(r)): n points r_km[i] (strictly increasing, > 0) and
+ * lambda_kmi[i] = sqrt(2) G_F n_e(r_i) in 1/km (> 0), host arrays copied in.  Required before the
+ * first evolve of such an instance (else XFLAT_ERR_STATE); XFLAT_ERR_STATE for another matter_kind,
+ * XFLAT_ERR_INVAL for bad points. */
+int xflat_set_matter_table(xflat_t h, uint32_t inst, const double* r_km, const double* lambda_kmi,
+                           uint32_t n);
 
 /* Put every beam of every instance back to the initial condition of Sec. 3.4 at radius r0_km. */
 int xflat_reset(xflat_t h, double r0_km);

@@ -42,3 +42,21 @@ class MeanSurvival(torch.autograd.Function):
 
 def mean_survival(N, theta, cfg, r0, r1, n_steps, checkpoint_every=64):
     return MeanSurvival.apply(N, theta, cfg, r0, r1, n_steps, checkpoint_every)
+
+
+def spectra_from_parameters(L, w, base):
+    """Per-bin number luminosities from the workload's parameters, as torch operations (so that
+    autograd carries gradients to them): L = (L_nue, L_nuebar, L_nux) (tensor of 3, the unit of
+    `base`), w = per-energy-bin multiplicative weights of the nu_e spectrum (tensor of n_energy),
+    base[s][f][k] = the per-bin number luminosity of a unit luminosity of species s (nu, nubar)
+    and flavour f (e, x).  N[0][0] = L_nue w base[0][0], N[1][0] = L_nuebar base[1][0],
+    N[s][1] = L_nux base[s][1] (the x flavours share one luminosity)."""
+    return torch.stack([torch.stack([L[0] * w * base[0, 0], L[2] * base[0, 1]]),
+                        torch.stack([L[1] * base[1, 0], L[2] * base[1, 1]])])
+
+
+def mean_survival_from_parameters(L, w, theta, base, cfg, r0, r1, n_steps, checkpoint_every=64):
+    """J = Pbar_ee(r1) as a differentiable function of the three luminosities, the n_energy nu_e
+    spectral weights and theta_v (see spectra_from_parameters and MeanSurvival)."""
+    return MeanSurvival.apply(spectra_from_parameters(L, w, base), theta, cfg, r0, r1, n_steps,
+                              checkpoint_every)

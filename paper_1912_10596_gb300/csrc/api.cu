@@ -38,6 +38,7 @@ struct HostInst {
   std::vector<double> u, du;
   std::vector<double> N;                  // [2][nf][ne]
   bool spectra = false;
+  std::vector<double> mtab;               // matter table [n][3]: r_i, lambda_i, exponent p_i
   uint32_t e_off = 0, a_off = 0;
 };
 
@@ -70,6 +71,7 @@ struct xflat_s {
   int* d_words = nullptr;                  // [0] status, [1] all_done
   int* h_words = nullptr;                  // pinned mirror
   double* d_stage = nullptr;               // staging for conversions
+  double* d_mtab = nullptr;                // every instance's matter table, concatenated
   size_t stage_bytes = 0;
   // host mirrors
   std::vector<InstConst> ic;
@@ -138,7 +140,14 @@ int check_config(const xflat_config& c, std::string& why) {
   if (c.integrator == XFLAT_LIE_ADAPTIVE && c.n_phi >= 2) {
     why = "the adaptive Lie integrator is built for the bulb model only"; return XFLAT_ERR_UNSUPPORTED;
   }
-  if (c.matter_kind > 2) { why = "unknown matter_kind"; return XFLAT_ERR_INVAL; }
+  if (c.matter_kind > 3) { why = "unknown matter_kind"; return XFLAT_ERR_INVAL; }
+  if (c.geometry > 2) { why = "unknown geometry"; return XFLAT_ERR_INVAL; }
+  if (c.geometry != XFLAT_GEOMETRY_BULB && c.n_phi >= 2) {
+    why = "the extended bulb model has the bulb geometry only"; return XFLAT_ERR_UNSUPPORTED;
+  }
+  if (c.geometry == XFLAT_GEOMETRY_HOMOGENEOUS && !is_fin(c.mu_const_kmi)) {
+    why = "mu_const_kmi must be finite"; return XFLAT_ERR_INVAL;
+  }
   if (!(c.R_km > 0) || !is_fin(c.R_km)) { why = "R_km must be > 0"; return XFLAT_ERR_INVAL; }
   if (!(c.E_min_MeV > 0) || !(c.E_max_MeV > c.E_min_MeV) || !is_fin(c.E_max_MeV)) { why = "need 0 < E_min < E_max"; return XFLAT_ERR_INVAL; }
   for (int i = 0; i < 2; ++i) if (!is_fin(c.dm2_eV2[i])) { why = "dm2 not finite"; return XFLAT_ERR_INVAL; }
@@ -367,6 +376,8 @@ void fill_inst_const(HostInst& I, InstConst& ic) {
   ic.power = c.power;
   ic.lam_coef = c.matter_kind == XFLAT_MATTER_POWER_LAW ? kSqrt2GFhc2 * c.Ye * c.rho0_gcc / kMuG * 1e15 : 0.0;
   ic.lam_const = c.lambda_const_kmi;
+  ic.geom = (int)c.geometry;
+  ic.mu_const = c.mu_const_kmi;
   ic.B[0] = std::sin(2 * c.theta[0]);
   ic.B[1] = 0.0;
   ic.B[2] = -std::cos(2 * c.theta[0]);
@@ -710,6 +721,8 @@ int do_evolve(xflat_t h, const double* r1, bool sync_loop, uint32_t max_steps, i
   bool any = false, changed = !h->moments_valid;
   for (size_t i = 0; i < h->inst.size(); ++i) {
     if (!h->inst[i].spectra) return fail(h, XFLAT_ERR_STATE, "set_spectra before evolve");
+    if (h->inst[i].cfg.matter_kind == XFLAT_MATTER_TABLE && h->inst[i].mtab.empty())
+      return fail(h, XFLAT_ERR_STATE, "xflat_set_matter_table before evolve");
     InstDyn& d = h->dyn[i];
     const xflat_config& c = h->inst[i].cfg;
     const double target = r1 ? r1[i] : d.r_end;
@@ -911,11 +924,61 @@ int xflat_destroy(xflat_t h) {
   drop_graph(h);
   void* ptrs[] = {h->planes, h->escr, h->kst, h->d_ic, h->d_dyn, h->d_pieces, h->d_blk, h->d_acc, h->d_errmax,
                   h->d_nonfinite, h->d_etab, h->d_u, h->d_du, h->d_bar, h->d_words, h->d_stage,
-                  h->d_trace};
+                  h->d_trace, h->d_mtab};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->h_words) cudaFreeHost(h->h_words);
   delete h;
+  return XFLAT_OK;
+}
+
+// Upload every instance's matter table into one device array and point the instance constants
+// at their rows (the array is replaced whenever a table changes).
+int upload_matter_tables(xflat_t h) {
+  std::vector<double> all;
+  std::vector<size_t> off(h->inst.size());
+  for (size_t i = 0; i < h->inst.size(); ++i) {
+    off[i] = all.size();
+    all.insert(all.end(), h->inst[i].mtab.begin(), h->inst[i].mtab.end());
+  }
+  if (h->d_mtab) cudaFree(h->d_mtab);
+  h->d_mtab = nullptr;
+  if (!all.empty()) {
+    if (cudaMalloc(&h->d_mtab, all.size() * sizeof(double)) != cudaSuccess)
+      return fail(h, XFLAT_ERR_NOMEM, "matter table");
+    CUDA_TRY(h, cudaMemcpy(h->d_mtab, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  for (size_t i = 0; i < h->inst.size(); ++i) {
+    h->ic[i].mt_n = (int32_t)(h->inst[i].mtab.size() / 3);
+    h->ic[i].mtab = h->ic[i].mt_n ? h->d_mtab + off[i] : nullptr;
+  }
+  return upload_inst(h);
+}
+
+int xflat_set_matter_table(xflat_t h, uint32_t inst, const double* r_km, const double* lambda_kmi,
+                           uint32_t n) {
+  if (!h) return XFLAT_ERR_INVAL;
+  if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
+  HostInst& I = h->inst[inst];
+  if (I.cfg.matter_kind != XFLAT_MATTER_TABLE) return fail(h, XFLAT_ERR_STATE, "matter_kind is not XFLAT_MATTER_TABLE");
+  if (!r_km || !lambda_kmi || n < 1) return fail(h, XFLAT_ERR_INVAL, "need n >= 1 points");
+  for (uint32_t i = 0; i < n; ++i) {
+    if (!is_fin(r_km[i]) || !(r_km[i] > 0) || !is_fin(lambda_kmi[i]) || !(lambda_kmi[i] > 0))
+      return fail(h, XFLAT_ERR_INVAL, "table radii and strengths must be finite and > 0");
+    if (i && !(r_km[i] > r_km[i - 1])) return fail(h, XFLAT_ERR_INVAL, "table radii must increase");
+  }
+  std::vector<double> t(3ull * n);
+  for (uint32_t i = 0; i < n; ++i) {
+    t[3 * i] = r_km[i];
+    t[3 * i + 1] = lambda_kmi[i];
+    t[3 * i + 2] = i + 1 < n ? std::log(lambda_kmi[i + 1] / lambda_kmi[i]) / std::log(r_km[i + 1] / r_km[i]) : 0.0;
+  }
+  I.mtab = t;
+  int rc;
+  if ((rc = download_dyn(h))) return rc;
+  if ((rc = upload_matter_tables(h))) return rc;
+  // the stage strengths of the current step were computed with the previous profile
+  h->moments_valid = false;
   return XFLAT_OK;
 }
 
@@ -1238,8 +1301,10 @@ int xflat_get_stats(xflat_t h, xflat_stats* out) { return xflat_get_stats_inst(h
 int xflat_adjoint(xflat_t h, double r0_km, double r1_km, uint32_t n_steps, uint32_t checkpoint_every,
                   double* dJ_dN, double* dJ_dtheta, double* J_out) {
   if (!h) return XFLAT_ERR_INVAL;
-  if (h->nf != 2 || h->inst.size() != 1 || h->extended)
-    return fail(h, XFLAT_ERR_UNSUPPORTED, "the adjoint is built for one two-flavour bulb-model instance");
+  if (h->nf != 2 || h->inst.size() != 1 || h->extended || h->inst[0].cfg.geometry != XFLAT_GEOMETRY_BULB ||
+      h->inst[0].cfg.matter_kind == XFLAT_MATTER_TABLE)
+    return fail(h, XFLAT_ERR_UNSUPPORTED,
+                "the adjoint is built for one two-flavour bulb-model instance (bulb geometry, no matter table)");
   HostInst& I = h->inst[0];
   if (!I.spectra) return fail(h, XFLAT_ERR_STATE, "set_spectra before the adjoint");
   if (!is_fin(r0_km) || !is_fin(r1_km) || r0_km < I.cfg.R_km || !(r1_km > r0_km))

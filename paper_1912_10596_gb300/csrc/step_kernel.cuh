@@ -168,14 +168,33 @@ template <typename Real>
 __host__ __device__ constexpr Real rbig() { return sizeof(Real) == 4 ? Real(3.0e38) : Real(1.7e308); }
 
 // Geometry of one (stage radius, angle bin): cos, 1/cos, 1 - cos, 1/cos - 1 without cancellation.
+// The kernels use q (path-length factor 1/cos of Eq. eom), t1 (the weight of the moment D) and t2
+// (the factor of mu J1 in the nu-nu term): K = q [eta omega B + lambda z + mu (D + t2 J1)].
+//   bulb: q = 1/cos th, t1 = 1/cos th - 1, t2 = 1 - cos th (Eq. Hnu with the measure in u-bins);
+//   single angle: every beam radial (q = 1, D = 0) and t2 = (1 - sqrt(1 - x))^2 / x, the
+//     geometric factor of Eq. Hnu integrated over emission uniform in u (x = R^2 / r^2);
+//   homogeneous test geometry: q = 1, D = 0, t2 = 1 (H_nunu = mu0 J1, mu0 constant).
 struct Geo { double q, t1, t2; };
-__device__ __forceinline__ Geo geometry(double u, double x) {
+__device__ __forceinline__ Geo geometry(double u, double x, int geom = kGeomBulb) {
+  if (geom == kGeomSingleAngle) {
+    const double s = 1.0 + sqrt(1.0 - x);       // (1 - sqrt(1 - x))^2 / x = x / (1 + sqrt(1 - x))^2
+    return {1.0, 0.0, x / (s * s)};
+  }
+  if (geom == kGeomHomogeneous) return {1.0, 0.0, 1.0};
   const double c = sqrt(fma(-u, x, 1.0));
   const double t2 = u * x / (1.0 + c);          // 1 - cos
   const double q = 1.0 / c;                     // 1 / cos
   return {q, t2 * q, t2};                       // t1 = 1/cos - 1 = (1 - cos)/cos
 }
-__device__ __forceinline__ void geometry_f(double u, double x, float& q, float& t1, float& t2) {
+__device__ __forceinline__ void geometry_f(double u, double x, float& q, float& t1, float& t2,
+                                           int geom = kGeomBulb) {
+  if (geom != kGeomBulb) {
+    const Geo g = geometry(u, x, geom);
+    q = (float)g.q;
+    t1 = (float)g.t1;
+    t2 = (float)g.t2;
+    return;
+  }
   const float om = (float)fma(-u, x, 1.0);      // 1 - u x in double (no cancellation), then FP32
   const float ux = (float)(u * x);
   const float c = sqrtf(om);
@@ -258,7 +277,7 @@ struct Phys2 {
   static constexpr int NC = 3, NM = kNM2, NSC = kNSC2, KT = kF32 ? 24 : 8;
   enum : int { vT1 = 0, vQ = 1, vQBX = 2, vQBZ = 3, vG0X = 4, vG0Y = 5, vG0Z = 6,
                vNQBX = 7, vNQBZ = 8, vNG0X = 9, vNG0Y = 10, vNG0Z = 11 };
-  struct Consts { double B[3]; };
+  struct Consts { double B[3]; int geom; };
   struct Beam { Real eo; Real w; };   // eta * omega_k, signed weight du_j * g_{sigma,k}
 
   __device__ static inline Real val(const Real* t, int v) { return kF32 ? t[2 * v] : t[v]; }
@@ -326,10 +345,10 @@ struct Phys2 {
                                          const Consts& C, int, int) {
     if constexpr (kF32) {
       float q, t1v, t2;
-      geometry_f(u, x, q, t1v, t2);
+      geometry_f(u, x, q, t1v, t2, C.geom);
       fill_f(row, q, t1v, t2, reinterpret_cast<const float*>(scr), C);
     } else {
-      fill(row, geometry(u, x), sc, C);
+      fill(row, geometry(u, x, C.geom), sc, C);
     }
   }
   // Frobenius norm^2 of the traceless part of P = (1 + s.sigma)/2: |s|^2 / 2
@@ -363,7 +382,7 @@ template <typename Real>
 struct Phys3 {
   static constexpr bool kPairable = false;
   static constexpr int NC = 9, NM = kNM3, NSC = kNSC3, KT = 4;
-  struct Consts { double M21[6], M31[6]; };
+  struct Consts { double M21[6], M31[6]; int geom; };
   struct Beam { Real o21, o31; Real w; };
 
   __device__ static inline Real t1(const Real* t) { return t[1]; }
@@ -464,10 +483,10 @@ struct Phys3 {
                                          const Consts& C, int, int) {
     if constexpr (sizeof(Real) == 4) {
       float q, t1v, t2;
-      geometry_f(u, x, q, t1v, t2);
+      geometry_f(u, x, q, t1v, t2, C.geom);
       fill_f(row, q, t1v, t2, reinterpret_cast<const float*>(scr), C);
     } else {
-      fill(row, geometry(u, x), sc, C);
+      fill(row, geometry(u, x, C.geom), sc, C);
     }
   }
 };
@@ -647,14 +666,28 @@ __device__ __forceinline__ double controller_factor(double err) {
 
 // mu(r) and lambda(r) at one radius (double).
 // mu(r) and lambda(r) from 1/r
+// lambda(r) from a matter table: the interval [r_i, r_{i+1}) holding r by binary search, then
+// lambda_i (r / r_i)^p_i (the end values outside the table)
+__device__ inline double table_strength(const double* t, int n, double r) {
+  if (r <= t[0]) return t[1];
+  if (r >= t[3 * (n - 1)]) return t[3 * (n - 1) + 1];
+  int lo = 0, hi = n - 1;                       // t[3 lo] <= r < t[3 hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (t[3 * mid] <= r) lo = mid; else hi = mid;
+  }
+  return t[3 * lo + 1] * pow(r / t[3 * lo], t[3 * lo + 2]);
+}
 __device__ __forceinline__ void strengths_inv(const InstConst& ic, double inv, double& mu, double& lam) {
-  mu = ic.mu_coef * inv * inv;
+  mu = ic.geom == kGeomHomogeneous ? ic.mu_const : ic.mu_coef * inv * inv;
   lam = 0.0;
   if (ic.matter == kMatterPower) {
     const double x = ic.r_ref * inv;
     lam = ic.lam_coef * (ic.power == 3.0 ? x * x * x : pow(x, ic.power));
   } else if (ic.matter == kMatterConst) {
     lam = ic.lam_const;
+  } else if (ic.matter == kMatterTable) {
+    lam = table_strength(ic.mtab, ic.mt_n, 1.0 / inv);
   }
 }
 __device__ __forceinline__ void strengths(const InstConst& ic, double r, double& mu, double& lam) {
@@ -1813,9 +1846,11 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     if constexpr (Phys::NC == 3) {
       C.B[0] = ic.B[0]; C.B[1] = ic.B[1]; C.B[2] = ic.B[2];
       if constexpr (Phys::NM == 12) C.n_phi = (int)ic.n_phi;
+      else C.geom = ic.geom;
     } else {
 #pragma unroll
       for (int i = 0; i < 6; ++i) { C.M21[i] = ic.M21[i]; C.M31[i] = ic.M31[i]; }
+      C.geom = ic.geom;
     }
     // table rows: every needed stage, or (incremental) only the newest and the formed stage
     const unsigned fill = incremental ? (need & (3u << kNewest)) : need;

@@ -28,7 +28,8 @@ constexpr int kAccCopies = 8;
 constexpr int kAccWordsPerInst = kMaxStages * kAccCopies * kNMMax * 2;
 
 enum Integrator : int { kRK4 = 0, kDP45 = 1, kLieRK4 = 2, kExpMid = 3, kLieAdaptive = 4 };
-enum Matter : int { kMatterNone = 0, kMatterPower = 1, kMatterConst = 2 };
+enum Matter : int { kMatterNone = 0, kMatterPower = 1, kMatterConst = 2, kMatterTable = 3 };
+enum Geometry : int { kGeomBulb = 0, kGeomSingleAngle = 1, kGeomHomogeneous = 2 };
 
 // Instance constants, written by the host before a launch.
 struct InstConst {
@@ -43,6 +44,10 @@ struct InstConst {
   double wscale;            // physical per-bin number luminosity of a unit table weight (1/s)
   double acc_unit;          // mixed kernels: value of one unit of the fixed-point moment sums (2^-S)
   double lam_coef, power, lam_const, r_ref;   // lambda(r) = lam_coef (r_ref / r)^power
+  const double* mtab;       // matter table: [mt_n][3] (r_i, lambda_i, exponent p_i of the interval
+  int32_t mt_n;             // after r_i: lambda = lambda_i (r/r_i)^p_i), device memory, or null
+  int32_t geom;             // Geometry
+  double mu_const;          // homogeneous geometry: the constant nu-nu strength mu0 (1/km)
   int32_t matter;
   int32_t adaptive;
   double B[3];              // 2 flavours: unit vacuum vector (sin 2th, 0, -cos 2th)

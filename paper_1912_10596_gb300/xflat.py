@@ -14,16 +14,19 @@ if not os.path.exists(_LIB_PATH):
     raise ImportError(f"{_LIB_PATH} is missing: run `python -c 'import __graft_entry__ as g; g.build()'`")
 _lib = C.CDLL(_LIB_PATH)
 
-ABI_VERSION = 1
+ABI_VERSION = 2
 OK, ERR_INVAL, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_STEP, ERR_STATE, ERR_UNSUPPORTED = range(9)
 FP64, MIXED = 0, 1
 RK4, DP45, LIE_RK4, EXP_MIDPOINT, LIE_ADAPTIVE = 0, 1, 2, 3, 4
-MATTER_NONE, MATTER_POWER_LAW, MATTER_CONSTANT = 0, 1, 2
+MATTER_NONE, MATTER_POWER_LAW, MATTER_CONSTANT, MATTER_TABLE = 0, 1, 2, 3
+GEOMETRY_BULB, GEOMETRY_SINGLE_ANGLE, GEOMETRY_HOMOGENEOUS = 0, 1, 2
 LAYOUT_MATRIX, LAYOUT_NATIVE = 0, 1
 
 _INTEGRATORS = {"rk4": RK4, "dp45": DP45, "lie_rk4": LIE_RK4, "exp_midpoint": EXP_MIDPOINT,
                 "lie_adaptive": LIE_ADAPTIVE}
-_MATTER = {"none": MATTER_NONE, "power_law": MATTER_POWER_LAW, "constant": MATTER_CONSTANT}
+_MATTER = {"none": MATTER_NONE, "power_law": MATTER_POWER_LAW, "constant": MATTER_CONSTANT,
+           "table": MATTER_TABLE}
+_GEOMETRY = {"bulb": GEOMETRY_BULB, "single_angle": GEOMETRY_SINGLE_ANGLE, "homogeneous": GEOMETRY_HOMOGENEOUS}
 _PRECISION = {"fp64": FP64, "mixed": MIXED}
 
 
@@ -40,7 +43,7 @@ class xflat_config(C.Structure):
         ("lambda_const_kmi", C.c_double),
         ("cuda_stream", C.c_void_p), ("barrier_timeout_ns", C.c_uint64),
         ("block_size", C.c_uint32), ("blocks_per_sm", C.c_uint32),
-        ("steps_per_launch", C.c_uint32), ("reserved1", C.c_uint32),
+        ("steps_per_launch", C.c_uint32), ("geometry", C.c_uint32), ("mu_const_kmi", C.c_double),
     ]
 
 
@@ -65,6 +68,7 @@ _SIGS = {
     "xflat_set_spectra": (_H, _P, _P, _P),
     "xflat_set_spectra_inst": (_H, C.c_uint32, _P, _P, _P),
     "xflat_reset": (_H, C.c_double),
+    "xflat_set_matter_table": (_H, C.c_uint32, _P, _P, C.c_uint32),
     "xflat_evolve": (_H, C.c_double, C.c_double),
     "xflat_evolve_batch": (_H, _P),
     "xflat_advance": (_H, _P, C.c_uint32, C.POINTER(C.c_int)),
@@ -145,6 +149,8 @@ def config_from_workload(wl, **over) -> xflat_config:
             v = _PRECISION[v]
         if k == "integrator" and isinstance(v, str):
             v = _INTEGRATORS[v]
+        if k == "geometry" and isinstance(v, str):
+            v = _GEOMETRY[v]
         setattr(c, k, v)
     return c
 
@@ -184,6 +190,11 @@ class Solver:
         u = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
         du = None if du is None else np.ascontiguousarray(du, dtype=np.float64)
         _check(_lib.xflat_set_spectra_inst(self.h, inst, _ptr(N), _ptr(u), _ptr(du)), self.h)
+
+    def set_matter_table(self, r_km, lambda_kmi, inst=0):
+        r = np.ascontiguousarray(r_km, dtype=np.float64)
+        lam = np.ascontiguousarray(lambda_kmi, dtype=np.float64)
+        _check(_lib.xflat_set_matter_table(self.h, inst, _ptr(r), _ptr(lam), len(r)), self.h)
 
     def reset(self, r0):
         _check(_lib.xflat_reset(self.h, r0), self.h)

@@ -35,6 +35,8 @@ def make_solver(xf, wl, grid=None, **over):
         s.set_spectra(g.N)
     else:
         s.set_spectra(g.N, g.u, g.du)
+    if wl.matter == "table":
+        s.set_matter_table(wl.matter_table_r, wl.matter_table_lambda)
     return s
 
 

@@ -42,8 +42,9 @@ def test_status_strings_and_defaults_without_gpu(lib_path):
     assert lib.xflat_status_string(4) == b"device barrier timeout"
     from paper_1912_10596_gb300 import xflat
     c = xflat.default_config()
-    assert c.abi_version == 1 and c.n_flavor == 2 and c.R_km == 11.0
-    assert ctypes.sizeof(xflat.xflat_config) == 216
+    assert c.abi_version == xflat.ABI_VERSION == 2 and c.n_flavor == 2 and c.R_km == 11.0
+    assert c.geometry == xflat.GEOMETRY_BULB and c.mu_const_kmi == 0.0
+    assert ctypes.sizeof(xflat.xflat_config) == 224
 
 
 def test_create_rejects_bad_config_before_touching_the_gpu(lib_path):
@@ -69,4 +70,14 @@ def test_create_rejects_bad_config_before_touching_the_gpu(lib_path):
     assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_UNSUPPORTED
     c = xflat.default_config()
     c.integrator = 5
+    assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_INVAL
+    c = xflat.default_config()
+    c.geometry = 3
+    assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_INVAL
+    c = xflat.default_config()
+    c.geometry = xflat.GEOMETRY_SINGLE_ANGLE
+    c.n_phi = 4
+    assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_UNSUPPORTED
+    c = xflat.default_config()
+    c.matter_kind = 4
     assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_INVAL

@@ -123,6 +123,43 @@ def test_autograd_function(xf):
     assert float(th.grad) == pytest.approx(2.0 * Gtho, rel=1e-8)
 
 
+def test_autograd_parameters_match_central_differences(xf):
+    """Gradients of J with respect to the three luminosities, the per-energy nu_e weights and
+    theta_v through autograd (the adjoint's dJ/dN carried through the spectra by torch) against
+    central differences of J itself."""
+    torch = pytest.importorskip("torch")
+    from paper_1912_10596_gb300.autograd import mean_survival_from_parameters
+    wl = Workload(name="adjp", n_energy=6, n_angle=5, integrator="rk4", n_steps=30)
+    cfg = xf.config_from_workload(wl)
+    unit = Workload(name="unit", n_energy=6, n_angle=5,
+                    L={k: 1e51 for k in ("nue", "nuebar", "nux", "nuxbar")})
+    base = torch.tensor(Grid.from_workload(unit).N, dtype=torch.float64)
+    L = torch.tensor([1.0, 1.3, 0.8], dtype=torch.float64, requires_grad=True)
+    w = torch.linspace(0.8, 1.2, 6, dtype=torch.float64).requires_grad_(True)
+    th = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+    J = mean_survival_from_parameters(L, w, th, base, cfg, 100.0, 102.0, 30, 8)
+    J.backward()
+
+    def J_at(Lv, wv, tv):
+        with torch.no_grad():
+            return float(mean_survival_from_parameters(Lv, wv, tv, base, cfg, 100.0, 102.0, 30, 8))
+
+    h = 1e-6
+    for i in range(3):
+        e = torch.zeros(3, dtype=torch.float64)
+        e[i] = h
+        fd = (J_at(L.detach() + e, w.detach(), th.detach()) - J_at(L.detach() - e, w.detach(), th.detach())) / (2 * h)
+        assert float(L.grad[i]) == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    for k in (0, 3, 5):
+        e = torch.zeros(6, dtype=torch.float64)
+        e[k] = h
+        fd = (J_at(L.detach(), w.detach() + e, th.detach()) - J_at(L.detach(), w.detach() - e, th.detach())) / (2 * h)
+        assert float(w.grad[k]) == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    fd = (J_at(L.detach(), w.detach(), th.detach() + h) - J_at(L.detach(), w.detach(), th.detach() - h)) / (2 * h)
+    assert abs(fd) > 1e-4
+    assert float(th.grad) == pytest.approx(fd, rel=1e-5)
+
+
 def test_adjoint_argument_checks(xf):
     wl = Workload(name="adj", n_energy=4, n_angle=3, integrator="rk4", n_steps=10)
     s = solver(xf, wl)
