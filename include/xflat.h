@@ -301,6 +301,44 @@ int xflat_get_stats_inst(xflat_t h, uint32_t inst, xflat_stats* out);
 int xflat_adjoint(xflat_t h, double r0_km, double r1_km, uint32_t n_steps, uint32_t checkpoint_every,
                   double* dJ_dN, double* dJ_dtheta, double* J_out);
 
+/* ---- one problem over several GPUs: beam shards --------------------------------------------------
+ * The paper splits the angle bins of one problem over MPI ranks and sums the integrals of Eq. F
+ * over all ranks at every evaluation of the right-hand side (Sec. 3.3).  A shard handle integrates
+ * the beams [beam_lo, beam_hi) of one instance (beam index as above; beam_lo a multiple of 4,
+ * beam_hi a multiple of 4 or n_beams) and runs one pass per launch; between passes the caller adds
+ * the shards' partial sums (exactly: they are fixed-point integers) and hands the totals back.  A
+ * radial integration to r1_km on every rank:
+ *   xflat_shard_begin(h, r1_km);
+ *   xflat_shard_pass(h, -1); exchange; xflat_shard_serial(h, 1, &done);       -- moments of the state
+ *   while (!done) for (p = 0; p < passes; ++p) {
+ *     xflat_shard_pass(h, p); exchange;                                       -- exchange = partials,
+ *     if (p == passes - 1) xflat_shard_serial(h, 0, &done);                       sum over shards,
+ *   }                                                                             set_totals
+ * The planes, tables and outputs of a shard handle span the whole instance, but only its own
+ * beams are integrated (get_rho / pee / flux on the other beams return the initial state); the
+ * moments it reports are those of its own beams.  xflat_evolve / xflat_advance return
+ * XFLAT_ERR_STATE on a shard handle.  With the same block decomposition (the shard boundaries on
+ * the unsharded handle's block boundaries) the result is bit-identical to the unsharded run. */
+int xflat_create_shard(const xflat_config* cfg, uint32_t beam_lo, uint32_t beam_hi, xflat_t* out);
+/* passes per radial step of the handle's integrator, and the length of the exchanged word vector */
+int xflat_shard_info(xflat_t h, uint32_t* passes_per_step, uint32_t* n_words);
+/* set the target radius (as xflat_evolve) without launching anything */
+int xflat_shard_begin(xflat_t h, double r1_km);
+/* the beam work of pass `pass` (0 .. passes-1) of the current step, or (-1) the moments of the
+ * current state, on this shard's beams; enqueued on the handle's stream */
+int xflat_shard_pass(xflat_t h, int32_t pass);
+/* words [n_words] (host): the last pass's partial moments as 128-bit two's-complement fixed-point
+ * integers (lo, hi) per component, then the bits of its error maximum (a non-negative double; the
+ * total is the maximum over shards) and its non-finite flag (the total is the logical or).
+ * Synchronises the stream. */
+int xflat_shard_partials(xflat_t h, int64_t* words);
+/* the totals over all shards, same layout, in place of this shard's partials */
+int xflat_shard_set_totals(xflat_t h, const int64_t* words);
+/* the serial section after the moment pass (after_moment_pass = 1) or after a step's final pass
+ * (0): stage constants, step-size control, the next step's geometry.  *done_out (nullable): every
+ * target reached.  Synchronises the stream; returns the device status. */
+int xflat_shard_serial(xflat_t h, int32_t after_moment_pass, int* done_out);
+
 /* ---- allocation-free moments (the paper has no counterpart: an addition for callers) ------------ */
 
 #define XFLAT_NOALLOC_MAX_ANGLES 4096u

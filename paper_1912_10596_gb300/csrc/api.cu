@@ -93,6 +93,13 @@ struct xflat_s {
   uint32_t graph_launches = 0, graph_steps = 0;
   bool moments_valid = false;
   bool advancing = false;                  // last call was an xflat_advance launch
+  // beam shard of one instance (xflat_create_shard): the handle integrates beams [shard_lo,
+  // shard_hi) only, one pass per launch, and the host exchanges the stage moments between passes
+  bool shard = false;
+  uint32_t shard_lo = 0, shard_hi = 0;
+  // dynamic piece scheduling (several instances): blocks take pieces from a device-wide counter
+  bool dyn_sched = false;
+  int shard_last = -2;                     // the last pass launched (-1: moment pass), -2: none
   std::string err;
 };
 
@@ -450,16 +457,50 @@ void reset_dyn(xflat_t h, uint32_t i, double r0) {
 }
 
 // Cut all instances into G slices and slices into pieces; blk[b]..blk[b+1] are block b's pieces.
+// Dynamic scheduling: every instance's beams cut into pieces of about kDynChunk vector iterations
+// per thread (and at most the table's rows); blocks take them in order from a counter.
+constexpr uint32_t kDynChunk = 32;
+void build_dynamic_pieces(xflat_t h) {
+  h->pieces.clear();
+  h->blk.assign(h->grid + 1, 0);
+  h->max_jj = 1;
+  const uint64_t chunk = (uint64_t)kDynChunk * 2 * h->block;
+  for (uint32_t i = 0; i < h->inst.size(); ++i) {
+    const HostInst& I = h->inst[i];
+    const uint32_t ne = I.cfg.n_energy;
+    const uint64_t rows_cap = std::max<uint64_t>(kAlignBeams, ((uint64_t)(max_jj_cap(h->nf, h->real_size, h->extended) - 1) * ne) / kAlignBeams * kAlignBeams);
+    const uint64_t len = std::min<uint64_t>(chunk, rows_cap);
+    for (uint64_t a = 0; a < I.n_beams; a += len) {
+      Piece p{};
+      p.inst = (int)i;
+      p.start = (uint32_t)a;
+      p.len = (uint32_t)std::min<uint64_t>(len, I.n_beams - a);
+      p.jj_lo = p.start / ne;
+      p.n_jj = (p.start + p.len - 1) / ne - p.jj_lo + 1;
+      h->max_jj = std::max<int>(h->max_jj, (int)p.n_jj);
+      h->pieces.push_back(p);
+    }
+  }
+}
+
 void build_pieces(xflat_t h, int G) {
-  uint64_t T = 0;
+  if (h->dyn_sched) {
+    build_dynamic_pieces(h);
+    return;
+  }
+  uint64_t T = 0, A = 0;                   // the beams [A, A + T) of the planes the grid covers
   for (auto& I : h->inst) T = std::max<uint64_t>(T, I.off + I.n_pad);
+  if (h->shard) {
+    A = h->inst[0].off + h->shard_lo;
+    T = h->shard_hi - h->shard_lo;
+  }
   h->pieces.clear();
   h->blk.assign(G + 1, 0);
   h->max_jj = 1;
   for (int b = 0; b < G; ++b) {
     h->blk[b] = (int)h->pieces.size();
-    uint64_t s0 = (T * (uint64_t)b / G) / kAlignBeams * kAlignBeams;
-    uint64_t s1 = (b == G - 1) ? T : (T * (uint64_t)(b + 1) / G) / kAlignBeams * kAlignBeams;
+    uint64_t s0 = A + (T * (uint64_t)b / G) / kAlignBeams * kAlignBeams;
+    uint64_t s1 = A + ((b == G - 1) ? T : (T * (uint64_t)(b + 1) / G) / kAlignBeams * kAlignBeams);
     for (uint32_t i = 0; i < h->inst.size(); ++i) {
       const HostInst& I = h->inst[i];
       const uint64_t lo = std::max<uint64_t>(s0, I.off), hi = std::min<uint64_t>(s1, I.off + I.n_beams);
@@ -532,15 +573,20 @@ KParams make_params(xflat_t h, int n_steps, int init_only) {
   p.max_jj = h->max_jj;
   p.integrator = h->integrator;
   p.trace = init_only ? nullptr : h->d_trace;
+  p.dyn_sched = h->dyn_sched ? 1 : 0;
   p.trace_passes = (int)h->trace_passes;
   return p;
 }
 
-int launch(xflat_t h, int n_steps, int init_only, cudaStream_t stream) {
+int launch(xflat_t h, int n_steps, int init_only, cudaStream_t stream, int shard_mode = kShardOff,
+           int shard_pass = 0) {
   KParams p = make_params(h, n_steps, init_only);
+  p.shard_mode = shard_mode;
+  p.shard_pass = shard_pass;
   void* args[] = {&p};
   cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(h->grid);
+  const bool serial_only = shard_mode == kShardSerialInit || shard_mode == kShardSerialFinal;
+  cfg.gridDim = dim3(serial_only ? 1 : h->grid);
   cfg.blockDim = dim3(h->block);
   cfg.dynamicSmemBytes = h->smem;
   cfg.stream = stream;
@@ -678,13 +724,17 @@ int setup_launch_shape(xflat_t h, const xflat_config& c) {
   if (c.blocks_per_sm) occ = std::min<int>(occ, (int)c.blocks_per_sm);
   uint64_t T = 0;
   for (auto& I : h->inst) T += I.n_pad;
+  if (h->shard) T = h->shard_hi - h->shard_lo;
   int G = occ * h->sm_count;
   // at least one vector of work per thread
   const uint64_t per_block = (uint64_t)h->block * kAlignBeams;
   G = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)G, (T + per_block - 1) / per_block));
   h->grid = G;
+  h->dyn_sched = h->inst.size() > 1 && !h->shard;
   build_pieces(h, G);
   h->smem = smem_bytes(h->nf, h->real_size, h->max_jj, table_stages(h->integrator), h->extended);
+  if (h->d_pieces) cudaFree(h->d_pieces);
+  if (h->d_blk) cudaFree(h->d_blk);
   CUDA_TRY(h, cudaMalloc(&h->d_pieces, sizeof(Piece) * std::max<size_t>(1, h->pieces.size())));
   CUDA_TRY(h, cudaMalloc(&h->d_blk, sizeof(int) * h->blk.size()));
   CUDA_TRY(h, cudaMemcpy(h->d_pieces, h->pieces.data(), sizeof(Piece) * h->pieces.size(), cudaMemcpyHostToDevice));
@@ -707,18 +757,14 @@ void* cur_plane(xflat_t h, uint32_t i) {
   return (char*)h->planes + ((size_t)par * h->nc * h->stride + h->inst[i].off) * h->real_size;
 }
 
-int do_evolve(xflat_t h, const double* r1, bool sync_loop, uint32_t max_steps, int* done_out) {
+// Targets of an evolve or advance: per instance the radius r1 (null: the previous target), the
+// fixed-step grid or the adaptive state, and the current radius as stage 1; *any = some instance
+// still has work, *changed = the moments of the current state must be recomputed.
+int prepare_targets(xflat_t h, const double* r1, bool& any, bool& changed) {
   int rc;
-  if (!sync_loop && r1 == nullptr && h->moments_valid && h->advancing) {
-    // continuing an advance: device state, moments and step geometry are already in place
-    if (done_out) *done_out = h->h_words[1];
-    if ((rc = launch(h, (int)max_steps, 0))) return rc;
-    CUDA_TRY(h, cudaMemcpyAsync(h->h_words, h->d_words, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    return XFLAT_OK;
-  }
-  h->advancing = false;
   if ((rc = download_dyn(h))) return rc;
-  bool any = false, changed = !h->moments_valid;
+  any = false;
+  changed = !h->moments_valid;
   for (size_t i = 0; i < h->inst.size(); ++i) {
     if (!h->inst[i].spectra) return fail(h, XFLAT_ERR_STATE, "set_spectra before evolve");
     if (h->inst[i].cfg.matter_kind == XFLAT_MATTER_TABLE && h->inst[i].mtab.empty())
@@ -750,6 +796,22 @@ int do_evolve(xflat_t h, const double* r1, bool sync_loop, uint32_t max_steps, i
     d.xs[1] = h->ic[i].R2 / (d.r * d.r);
     any = any || !d.done;
   }
+  return XFLAT_OK;
+}
+
+int do_evolve(xflat_t h, const double* r1, bool sync_loop, uint32_t max_steps, int* done_out) {
+  int rc;
+  if (h->shard) return fail(h, XFLAT_ERR_STATE, "a beam-shard handle advances with the xflat_shard_* calls");
+  if (!sync_loop && r1 == nullptr && h->moments_valid && h->advancing) {
+    // continuing an advance: device state, moments and step geometry are already in place
+    if (done_out) *done_out = h->h_words[1];
+    if ((rc = launch(h, (int)max_steps, 0))) return rc;
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_words, h->d_words, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    return XFLAT_OK;
+  }
+  h->advancing = false;
+  bool any = false, changed = false;
+  if ((rc = prepare_targets(h, r1, any, changed))) return rc;
   if (done_out) *done_out = any ? 0 : 1;
   if (!any) return XFLAT_OK;
   if ((rc = upload_dyn(h))) return rc;
@@ -1445,6 +1507,149 @@ int xflat_adjoint(xflat_t h, double r0_km, double r1_km, uint32_t n_steps, uint3
     *dJ_dtheta = t;
   }
   if (J_out) *J_out = J;
+  return XFLAT_OK;
+}
+
+// ---- beam shards: one problem over several GPUs (Sec. 3.3's decomposition of the angle bins and
+// the sum of the Eq. F integrals over ranks at every evaluation) ---------------------------------
+int xflat_create_shard(const xflat_config* cfg, uint32_t beam_lo, uint32_t beam_hi, xflat_t* out) {
+  if (!cfg || !out) return XFLAT_ERR_INVAL;
+  xflat_t h = nullptr;
+  int rc = create_impl(cfg, 1, &h);
+  if (rc) return rc;
+  const uint32_t nb = h->inst[0].n_beams;
+  if (!(beam_lo < beam_hi && beam_hi <= nb) || beam_lo % kAlignBeams != 0 ||
+      (beam_hi % kAlignBeams != 0 && beam_hi != nb)) {
+    xflat_destroy(h);
+    return XFLAT_ERR_INVAL;
+  }
+  h->shard = true;
+  h->shard_lo = beam_lo;
+  h->shard_hi = beam_hi;
+  h->ic[0].rec_start = beam_lo;
+  if ((rc = setup_launch_shape(h, *cfg)) || (rc = upload_inst(h))) {
+    xflat_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return XFLAT_OK;
+}
+
+int xflat_shard_info(xflat_t h, uint32_t* passes_per_step, uint32_t* n_words) {
+  if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
+  const int it = h->integrator;
+  const uint32_t passes = it == XFLAT_DP45 ? 7 : it == XFLAT_EXP_MIDPOINT ? 2 : it == XFLAT_LIE_ADAPTIVE ? 11 : 4;
+  const uint32_t nm = h->extended ? 12 : (h->nf == 2 ? kNM2 : kNM3);
+  if (passes_per_step) *passes_per_step = passes;
+  if (n_words) *n_words = 2 * nm + 2;
+  return XFLAT_OK;
+}
+
+int xflat_shard_begin(xflat_t h, double r1_km) {
+  if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
+  bool any = false, changed = false;
+  int rc;
+  if ((rc = prepare_targets(h, &r1_km, any, changed))) return rc;
+  if ((rc = upload_dyn(h))) return rc;
+  if ((rc = clear_sync_words(h))) return rc;
+  h->shard_last = -2;
+  h->moments_valid = false;
+  return XFLAT_OK;
+}
+
+int xflat_shard_pass(xflat_t h, int32_t pass) {
+  if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
+  uint32_t passes = 0;
+  xflat_shard_info(h, &passes, nullptr);
+  if (pass < -1 || pass >= (int32_t)passes) return fail(h, XFLAT_ERR_INVAL, "pass out of range");
+  int rc;
+  if ((rc = launch(h, 0, 0, h->stream, kShardPass, pass))) return rc;
+  h->shard_last = pass;
+  return XFLAT_OK;
+}
+
+// The accumulator slot the last pass reduced into: the moment pass slot 1, stage pass p slot p + 2,
+// the final pass slot 0 (the new state's moments, where the integrator forms them).
+int shard_slot(xflat_t h) {
+  uint32_t passes = 0;
+  xflat_shard_info(h, &passes, nullptr);
+  if (h->shard_last == -1) return 1;
+  return h->shard_last == (int)passes - 1 ? 0 : h->shard_last + 2;
+}
+
+int xflat_shard_partials(xflat_t h, int64_t* words) {
+  if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
+  if (!words) return fail(h, XFLAT_ERR_INVAL, "words is NULL");
+  if (h->shard_last < -1) return fail(h, XFLAT_ERR_STATE, "no pass launched");
+  uint32_t nw = 0;
+  xflat_shard_info(h, nullptr, &nw);
+  const int nm = (int)(nw - 2) / 2, slot = shard_slot(h);
+  constexpr int kWords = kAccCopies * kNMMax * 2;
+  std::vector<unsigned long long> acc(kWords);
+  unsigned long long em = 0;
+  int nonfin = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(acc.data(), h->d_acc + (size_t)slot * kWords, kWords * 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(&em, h->d_errmax, 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(&nonfin, h->d_nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < nm; ++c) {
+    unsigned __int128 t = 0;
+    for (int cp = 0; cp < kAccCopies; ++cp) {
+      const unsigned long long* w = acc.data() + ((size_t)cp * kNMMax + c) * 2;
+      if (h->real_size == 4) t += (unsigned __int128)(__int128)(long long)w[0];   // one signed word
+      else t += ((unsigned __int128)w[1] << 64) | (unsigned __int128)w[0];
+    }
+    words[2 * c] = (int64_t)(unsigned long long)t;
+    words[2 * c + 1] = (int64_t)(unsigned long long)(t >> 64);
+  }
+  words[2 * nm] = (int64_t)em;
+  words[2 * nm + 1] = nonfin;
+  return XFLAT_OK;
+}
+
+int xflat_shard_set_totals(xflat_t h, const int64_t* words) {
+  if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
+  if (!words) return fail(h, XFLAT_ERR_INVAL, "words is NULL");
+  if (h->shard_last < -1) return fail(h, XFLAT_ERR_STATE, "no pass launched");
+  uint32_t nw = 0;
+  xflat_shard_info(h, nullptr, &nw);
+  const int nm = (int)(nw - 2) / 2, slot = shard_slot(h);
+  constexpr int kWords = kAccCopies * kNMMax * 2;
+  std::vector<unsigned long long> acc(kWords, 0ull);    // the total in copy 0, the other copies 0
+  for (int c = 0; c < nm; ++c) {
+    acc[(size_t)c * 2] = (unsigned long long)words[2 * c];
+    acc[(size_t)c * 2 + 1] = h->real_size == 4 ? 0ull : (unsigned long long)words[2 * c + 1];
+    if (h->real_size == 4) {
+      // a mixed accumulator is one signed 64-bit word: the total must fit it
+      const long long lo = words[2 * c], hi = words[2 * c + 1];
+      if (hi != (lo < 0 ? -1 : 0)) return fail(h, XFLAT_ERR_INVAL, "moment total out of range");
+    }
+  }
+  const unsigned long long em = (unsigned long long)words[2 * nm];
+  const int nonfin = words[2 * nm + 1] ? 1 : 0;
+  CUDA_TRY(h, cudaMemcpy(h->d_acc + (size_t)slot * kWords, acc.data(), kWords * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(h, cudaMemcpy(h->d_errmax, &em, 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(h, cudaMemcpy(h->d_nonfinite, &nonfin, sizeof(int), cudaMemcpyHostToDevice));
+  return XFLAT_OK;
+}
+
+int xflat_shard_serial(xflat_t h, int32_t after_moment_pass, int* done_out) {
+  if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
+  uint32_t passes = 0;
+  xflat_shard_info(h, &passes, nullptr);
+  const bool init = after_moment_pass != 0;
+  if (init ? h->shard_last != -1 : h->shard_last != (int)passes - 1)
+    return fail(h, XFLAT_ERR_STATE, "the serial section follows the moment pass or a step's final pass");
+  int rc;
+  if ((rc = launch(h, 0, 0, h->stream, init ? kShardSerialInit : kShardSerialFinal, 0))) return rc;
+  int st, ad;
+  if ((rc = read_words(h, st, ad))) return rc;
+  h->moments_valid = true;
+  if (done_out) *done_out = ad;
+  if (st) {
+    if ((rc = download_dyn(h))) return rc;
+    return fail(h, st, std::string("device status: ") + xflat_status_string(st));
+  }
   return XFLAT_OK;
 }
 

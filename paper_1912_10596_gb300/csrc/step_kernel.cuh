@@ -606,6 +606,17 @@ struct KParams {
   int* all_done;
   int n_steps;
   int init_only;
+  // beam-shard mode (one problem split over several GPUs, the host exchanging the stage moments):
+  // 0 off; kShardPass: only pass `shard_pass` of the current step (-1: the moment pass of the
+  // current state), no device-wide barrier, no serial section; kShardSerialInit / Final: only the
+  // serial section that follows the moment pass or a step's final pass (one block)
+  int shard_mode;
+  int shard_pass;
+  // dynamic scheduling (handles with several instances): instead of a fixed list of pieces per
+  // block, every block takes the next piece of the pass from a device-wide counter until none is
+  // left, so blocks whose pieces run slower (small angle rows, more set-ups, memory placement) do
+  // not hold the whole grid at the pass's barrier
+  int dyn_sched;
   int max_jj;
   int integrator;
   // optional pass trace (NULL: off): per pass and block, %globaltimer at pass start, after the
@@ -981,6 +992,7 @@ struct BlockShared {
   int parity;
   int flag;
   int pass_idx;                        // passes run by this block in this launch (pass trace)
+  int next_piece;                      // dynamic scheduling: the piece this block processes next
   int keep;                            // single-piece block: launch-invariant set-up already loaded
   unsigned int gen_seen;               // barrier generation this block arrived in
 };
@@ -1734,13 +1746,24 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
   // the stage whose moments the previous pass reduced (0: none of this step, its constants come
   // from the serial update of the previous step or of the moment launch)
   constexpr int kNewest = (kKind != kInitPass && kPass >= 1) ? kPass + 1 : 0;
-  const int b0 = p.blk_piece[blockIdx.x], b1 = p.blk_piece[blockIdx.x + 1];
+  const bool dyn = p.dyn_sched != 0;
+  const int b0 = dyn ? 0 : p.blk_piece[blockIdx.x], b1 = dyn ? 0 : p.blk_piece[blockIdx.x + 1];
   // A block with a single piece keeps its set-up in shared memory for the whole step: after pass
   // 0 only the newest stage's constants and the table rows of the newest and the formed stage
   // change (flags, step size, coefficients, radii, angle tables and older rows stay valid).
-  const bool single = b1 - b0 == 1;
-  const bool incremental = single && kNewest >= 1;
-  for (int pi = b0; pi < b1; ++pi) {
+  const bool single = !dyn && b1 - b0 == 1;
+  const bool incremental = single && kNewest >= 1 && !p.shard_mode;
+  for (int it = 0;; ++it) {
+    int pi = b0 + it;
+    if (dyn) {
+      __syncthreads();                           // next_piece of the previous piece has been read
+      if (threadIdx.x == 0) bs.next_piece = (int)atomicAdd(&p.bar->chunk[(bs.gen_seen >> 1) & 1u], 1u);
+      __syncthreads();
+      pi = bs.next_piece;
+      if (pi >= p.n_pieces) break;
+    } else if (pi >= b1) {
+      break;
+    }
     const Piece pc = p.pieces[pi];
     const InstConst& ic = p.ic[pc.inst];
     const InstDyn* d = p.dyn + pc.inst;
@@ -1755,11 +1778,11 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
         if (c < Phys::NM) {
           const double m = acc_component<Real>(accs, c, ic.acc_unit);
           v = ldcg(&d->mus[kNewest]) * m;
-          if (pc.start == 0) dw->mom[kNewest][c] = m;
+          if (pc.start == ic.rec_start) dw->mom[kNewest][c] = m;
         } else if (c == Phys::NM) {
           v = ldcg(&d->lams[kNewest]);
         }
-        if (pc.start == 0 && c <= Phys::NM) dw->sc[kNewest][c] = v;
+        if (pc.start == ic.rec_start && c <= Phys::NM) dw->sc[kNewest][c] = v;
         bs.scd[kNewest][c] = v;
         bs.scr[kNewest][c] = (Real)v;
       }
@@ -1788,11 +1811,11 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
         if (c < Phys::NM) {
           const double m = acc_component<Real>(accs, c, ic.acc_unit);
           v = ldcg(&d->mus[s]) * m;
-          if (pc.start == 0) dw->mom[s][c] = m;
+          if (pc.start == ic.rec_start) dw->mom[s][c] = m;
         } else if (c == Phys::NM) {
           v = ldcg(&d->lams[s]);
         }
-        if (pc.start == 0 && c <= Phys::NM) dw->sc[s][c] = v;
+        if (pc.start == ic.rec_start && c <= Phys::NM) dw->sc[s][c] = v;
       } else if ((need >> s) & 1u) {
         v = ldcg(&d->sc[s][c]);
       }
@@ -2124,6 +2147,8 @@ __device__ __forceinline__ bool pass_and_sync(const KParams& p, BlockShared<Real
       t[3] = (res & 0xf) == kBarLast ? 1ull : 0ull;
     }
   }
+  if ((res & 0xf) == kBarLast && p.dyn_sched && threadIdx.x == 0)
+    p.bar->chunk[((bs.gen_seen >> 1) + 1u) & 1u] = 0u;   // the next pass's piece counter (released below)
   if ((res & 0xf) == kBarLast && !kFinal) {
     // stage pass: every block derives the new stage's constants from the accumulators in its next
     // set-up (run_pass), so the barrier opens at once (a non-finite partial is reported by the
@@ -2163,6 +2188,20 @@ __device__ __forceinline__ bool all_passes(const KParams& p, BlockShared<Real, P
   }
 }
 
+// Beam-shard mode: the beam work of one pass chosen at run time (no barrier, no serial section).
+template <class Phys, class Tab, typename Real, bool kCF, int kPass>
+__device__ __forceinline__ void one_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned char* dyn_smem,
+                                         int which) {
+  if constexpr (kPass < Tab::kPasses) {
+    if (which == kPass) {
+      constexpr int kKind = kPass == Tab::kPasses - 1 ? kFinalPass : kStagePass;
+      run_pass<Phys, Tab, Real, kCF, kPass, kKind>(p, bs, dyn_smem);
+      return;
+    }
+    one_pass<Phys, Tab, Real, kCF, kPass + 1>(p, bs, dyn_smem, which);
+  }
+}
+
 // kThreads x kMinB: the block size and resident blocks per SM the register budget is sized for.
 // FP64 work runs on GB300's narrow FP64 pipe (about 1/68 of the FP32 rate), which one 256-thread
 // block per SM already keeps busy, so FP64 kernels are built for that (whole register file, no
@@ -2179,10 +2218,27 @@ __global__ void __launch_bounds__(kThreads, kMinB) step_kernel(KParams p) {
     bs.keep = 0;
     bs.gen_seen = ld_acquire(&p.bar->gen);        // later barriers track the generation locally
   }
+  if (p.shard_mode == kShardPass) {
+    if (p.shard_pass < 0) run_pass<Phys, Tab, Real, kCF, 0, kInitPass>(p, bs, dyn_smem);
+    else one_pass<Phys, Tab, Real, kCF, 0>(p, bs, dyn_smem, p.shard_pass);
+    return;
+  }
+  if (p.shard_mode == kShardSerialInit || p.shard_mode == kShardSerialFinal) {
+    // one block; the host has replaced the pass's partial sums by the totals over all shards
+    if (blockIdx.x != 0) return;
+    const bool init = p.shard_mode == kShardSerialInit;
+    const int mine = serial_update<Phys, Tab, Real>(p, init ? 1 : 0, !init, init);
+    const int all = __syncthreads_and(mine);
+    if (!init) clear_late_slots<Tab>(p);
+    serial_geometry<Tab>(p);
+    if (threadIdx.x == 0) *p.all_done = all;
+    return;
+  }
   if (p.init_only) {
     run_pass<Phys, Tab, Real, kCF, 0, kInitPass>(p, bs, dyn_smem);
     const int res = barrier_arrive(p.bar, gridDim.x, p.timeout_ns, p.status, &bs.flag, &bs.gen_seen);
     if ((res & 0xf) == kBarLast) {
+      if (p.dyn_sched && threadIdx.x == 0) p.bar->chunk[((bs.gen_seen >> 1) + 1u) & 1u] = 0u;
       const int mine = serial_update<Phys, Tab, Real>(p, 1, false, true);
       const int all = __syncthreads_and(mine);
       serial_geometry<Tab>(p);

@@ -30,6 +30,7 @@ constexpr int kAccWordsPerInst = kMaxStages * kAccCopies * kNMMax * 2;
 enum Integrator : int { kRK4 = 0, kDP45 = 1, kLieRK4 = 2, kExpMid = 3, kLieAdaptive = 4 };
 enum Matter : int { kMatterNone = 0, kMatterPower = 1, kMatterConst = 2, kMatterTable = 3 };
 enum Geometry : int { kGeomBulb = 0, kGeomSingleAngle = 1, kGeomHomogeneous = 2 };
+enum ShardMode : int { kShardOff = 0, kShardPass = 1, kShardSerialInit = 2, kShardSerialFinal = 3 };
 
 // Instance constants, written by the host before a launch.
 struct InstConst {
@@ -47,6 +48,8 @@ struct InstConst {
   const double* mtab;       // matter table: [mt_n][3] (r_i, lambda_i, exponent p_i of the interval
   int32_t mt_n;             // after r_i: lambda = lambda_i (r/r_i)^p_i), device memory, or null
   int32_t geom;             // Geometry
+  uint32_t rec_start;       // first beam of the instance this handle integrates (beam shards; else 0):
+                            // the block holding it records the stage moments and constants
   double mu_const;          // homogeneous geometry: the constant nu-nu strength mu0 (1/km)
   int32_t matter;
   int32_t adaptive;
@@ -89,7 +92,11 @@ struct Barrier {
   int abort;
   int timeout_hits;
   unsigned int extra;       // test hook: additional arrivals expected
-  int pad2[29];
+  // dynamic piece scheduling: the pass after barrier generation g (which steps by 2, bit 0 being a
+  // flag) takes pieces from chunk[(g >> 1) & 1]; the last block at a barrier zeroes the counter
+  // of the pass that follows it before the release
+  unsigned int chunk[2];
+  int pad2[27];
 };
 
 // ---------------------------------------------------------------------------------------------

@@ -8,7 +8,8 @@ one of two ways:
   exchanged (``instance_shards``);
 * one problem: each rank takes a contiguous range of the beam index (``beam_shards``); every
   integrator stage needs the moments of all beams, so the ranks exchange their partial moments
-  once per stage (``allreduce_fixed``).
+  once per stage (``allreduce_fixed``); ``evolve_sharded`` drives a beam-shard handle of the
+  library pass by pass with that exchange (``exchange_words``).
 
 The exchange is exact and deterministic: a partial moment is carried as the FP64 device
 accumulators' own 128-bit fixed-point pair (hi 2^64 + lo = trunc(x 2^64), lo an unsigned and hi a
@@ -115,3 +116,71 @@ def max_over_ranks(x: float, group=None) -> float:
     t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     return float(t.item())
+
+
+def sum_words(parts):
+    """Totals of the beam-shard word vectors of xflat_shard_partials: the (lo, hi) fixed-point
+    pairs added exactly, the error maxima (bit patterns of non-negative doubles) by maximum, the
+    non-finite flags by logical or."""
+    n = len(parts[0])
+    nm = (n - 2) // 2
+    out = [0] * n
+    for c in range(nm):
+        t = 0
+        for w in parts:
+            t += (int(w[2 * c + 1]) << 64) + (int(w[2 * c]) % TWO64)
+        lo = t % TWO64
+        out[2 * c] = lo - TWO64 if lo >= (1 << 63) else lo
+        out[2 * c + 1] = t >> 64
+    out[2 * nm] = max(int(w[2 * nm]) for w in parts)
+    out[2 * nm + 1] = 1 if any(int(w[2 * nm + 1]) for w in parts) else 0
+    return out
+
+
+def exchange_words(words, group=None):
+    """All-gather this rank's word vector over `group` (torch.distributed, any backend) and return
+    the totals (sum_words over the ranks in rank order: the same on every rank)."""
+    import torch
+    import torch.distributed as dist
+
+    mine = torch.tensor([int(v) for v in words], dtype=torch.int64)
+    if dist.get_backend(group) == "nccl":
+        mine = mine.cuda()
+    bufs = [torch.empty_like(mine) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(bufs, mine, group=group)
+    return sum_words([b.cpu().tolist() for b in bufs])
+
+
+def evolve_sharded(shards, r1, exchange=None):
+    """Integrate one problem to r1 with beam-shard handles (objects with the Solver shard_* calls):
+    `shards` is this process's handles (one per rank on several GPUs; several in one process to
+    emulate ranks on one device), `exchange(word vector) -> totals` the cross-process reduction of
+    this process's total (e.g. exchange_words; None: only the handles given).  Every pass runs on
+    every shard before the exchange, so no kernel ever waits for another.  Returns the number of
+    radial steps taken."""
+    def reduce(ws):
+        local = sum_words(ws)
+        return exchange(local) if exchange is not None else local
+
+    passes = shards[0].shard_info()[0]
+    for s in shards:
+        s.shard_begin(r1)
+    for s in shards:
+        s.shard_pass(-1)
+    tot = reduce([s.shard_partials() for s in shards])
+    done = False
+    for s in shards:
+        s.shard_set_totals(tot)
+        done = s.shard_serial(True)
+    steps = 0
+    while not done:
+        for p in range(passes):
+            for s in shards:
+                s.shard_pass(p)
+            tot = reduce([s.shard_partials() for s in shards])
+            for s in shards:
+                s.shard_set_totals(tot)
+        for s in shards:
+            done = s.shard_serial(False)
+        steps += 1
+    return steps

@@ -90,6 +90,13 @@ _SIGS = {
     "xflat_moments_2f_noalloc": (_P, C.c_uint32, C.c_uint32, _P, _P, _P, C.c_double, C.c_double,
                                  _P, _P),
     "xflat_debug_trace": (_H, C.c_uint32, _P, C.POINTER(C.c_uint32)),
+    "xflat_create_shard": (C.POINTER(xflat_config), C.c_uint32, C.c_uint32, C.POINTER(_H)),
+    "xflat_shard_info": (_H, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)),
+    "xflat_shard_begin": (_H, C.c_double),
+    "xflat_shard_pass": (_H, C.c_int32),
+    "xflat_shard_partials": (_H, _P),
+    "xflat_shard_set_totals": (_H, _P),
+    "xflat_shard_serial": (_H, C.c_int32, C.POINTER(C.c_int)),
 }
 NOALLOC_MAX_ANGLES = 4096
 for _name, _args in _SIGS.items():
@@ -156,9 +163,10 @@ def config_from_workload(wl, **over) -> xflat_config:
 
 
 class Solver:
-    """Owning wrapper of one xflat handle (one instance or a batch)."""
+    """Owning wrapper of one xflat handle (one instance or a batch; with `shard`, the beams
+    [lo, hi) of one instance, advanced by the shard_* calls)."""
 
-    def __init__(self, cfgs, stream=None):
+    def __init__(self, cfgs, stream=None, shard=None):
         if isinstance(cfgs, xflat_config):
             cfgs = [cfgs]
         arr = (xflat_config * len(cfgs))(*cfgs)
@@ -166,7 +174,12 @@ class Solver:
             for c in arr:
                 c.cuda_stream = stream
         self.h = _H()
-        _check(_lib.xflat_create_batch(arr, len(cfgs), C.byref(self.h)))
+        if shard is not None:
+            if len(cfgs) != 1:
+                raise ValueError("a beam shard belongs to one instance")
+            _check(_lib.xflat_create_shard(arr, int(shard[0]), int(shard[1]), C.byref(self.h)))
+        else:
+            _check(_lib.xflat_create_batch(arr, len(cfgs), C.byref(self.h)))
         self.cfgs = list(arr)
         self.n_inst = len(cfgs)
 
@@ -287,6 +300,32 @@ class Solver:
         _check(_lib.xflat_adjoint(self.h, r0, r1, n_steps, checkpoint_every, _ptr(dN), _ptr(dth),
                                   _ptr(J)), self.h)
         return float(J[0]), dN.reshape(2, c.n_flavor, c.n_energy), float(dth[0])
+
+    # ---- beam shards (see shard.evolve_sharded) ----
+    def shard_info(self):
+        p, n = C.c_uint32(0), C.c_uint32(0)
+        _check(_lib.xflat_shard_info(self.h, C.byref(p), C.byref(n)), self.h)
+        return p.value, n.value
+
+    def shard_begin(self, r1):
+        _check(_lib.xflat_shard_begin(self.h, r1), self.h)
+
+    def shard_pass(self, p):
+        _check(_lib.xflat_shard_pass(self.h, p), self.h)
+
+    def shard_partials(self):
+        w = np.zeros(self.shard_info()[1], dtype=np.int64)
+        _check(_lib.xflat_shard_partials(self.h, _ptr(w)), self.h)
+        return w
+
+    def shard_set_totals(self, w):
+        w = np.ascontiguousarray(w, dtype=np.int64)
+        _check(_lib.xflat_shard_set_totals(self.h, _ptr(w)), self.h)
+
+    def shard_serial(self, after_moment_pass):
+        done = C.c_int(0)
+        _check(_lib.xflat_shard_serial(self.h, 1 if after_moment_pass else 0, C.byref(done)), self.h)
+        return bool(done.value)
 
     def debug_barrier_extra(self, extra):
         _check(_lib.xflat_debug_barrier_extra(self.h, extra), self.h)

@@ -119,3 +119,71 @@ def test_fixed_point_format():
     a, b = shard.to_fixed(0.75), shard.to_fixed(0.5)
     assert shard.from_fixed(shard.fixed_add(a, b)) == 1.25
     assert shard.from_fixed(shard.fixed_add(shard.to_fixed(-0.25), shard.to_fixed(0.25))) == 0.0
+
+
+class FakeShard:
+    """A stand-in for a beam-shard handle on a CPU rank: each 'pass' contributes this shard's part
+    of fixed integer moments (and an error maximum), and the serial section finishes after a
+    fixed number of steps; it records the totals it was handed."""
+
+    def __init__(self, part, steps):
+        self.part, self.steps, self.seen = part, steps, []
+        self.step = 0
+
+    def shard_info(self):
+        return 3, 2 * self.part.shape[1] + 2
+
+    def shard_begin(self, r1):
+        self.step = 0
+
+    def shard_pass(self, p):
+        self.last = p
+
+    def shard_partials(self):
+        w = []
+        for c in range(self.part.shape[1]):
+            t = int(self.part[:, c].sum()) * (self.last + 2)
+            w += [t % shard.TWO64 - (shard.TWO64 if t % shard.TWO64 >= 1 << 63 else 0), t >> 64]
+        return w + [int(self.part.max()) * 0 + 7 + (self.last + 2), 0]
+
+    def shard_set_totals(self, w):
+        self.seen.append(list(w))
+
+    def shard_serial(self, init):
+        if not init:
+            self.step += 1
+        return self.step >= self.steps
+
+
+def _sharded_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"], os.environ["MASTER_PORT"] = "127.0.0.1", str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(5)
+        allp = rng.integers(-(1 << 60), 1 << 60, size=(64, 3))
+        lo, hi = shard.beam_shards(64, world, align=4)[rank]
+        fs = FakeShard(allp[lo:hi], steps=4)
+        steps = shard.evolve_sharded([fs], 150.0, exchange=lambda w: shard.exchange_words(w))
+        q.put((rank, steps, fs.seen))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_evolve_sharded_exchange_on_two_ranks():
+    """The pass-by-pass driver on two gloo ranks: every rank is handed the same totals, equal to the
+    one-rank totals of all beams (128-bit integer sums, error maximum by max), every pass."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_sharded_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = dict((r, (st, seen)) for r, st, seen in (q.get(timeout=120) for _ in ps))
+    for p in ps:
+        p.join(timeout=60)
+    rng = np.random.default_rng(5)
+    allp = rng.integers(-(1 << 60), 1 << 60, size=(64, 3))
+    one = FakeShard(allp, steps=4)
+    assert shard.evolve_sharded([one], 150.0) == 4
+    assert res[0][0] == res[1][0] == 4
+    assert res[0][1] == res[1][1] == one.seen
