@@ -73,6 +73,8 @@ struct xflat_s {
   double* d_stage = nullptr;               // staging for conversions
   double* d_mtab = nullptr;                // every instance's matter table, concatenated
   size_t stage_bytes = 0;
+  // allocation sizes in bytes (the checked build hands them to the kernel with the pointers)
+  size_t planes_bytes = 0, escr_bytes = 0, kst_bytes = 0, etab_bytes = 0, angle_bytes = 0;
   // host mirrors
   std::vector<InstConst> ic;
   std::vector<InstDyn> dyn;
@@ -533,16 +535,21 @@ int table_row_values(int nf, size_t real_size, bool ext = false) {
 // the extended model has ten times the rows per beam, so its rows are kept narrow and a block's
 // share of a 4M-beam problem (about 130 rows at two blocks per SM) fits one piece
 uint32_t max_jj_cap(int nf, size_t real_size, bool ext) {
-  if (nf == 2 && real_size == 4) return ext ? 160u : 64u;
+  if (nf == 2 && real_size == 4) return ext ? 160u : 48u;
   return kMaxJJ;
 }
 
-size_t smem_bytes(int nf, size_t real_size, int max_jj, int stages, bool ext = false) {
+// Dynamic shared memory of a step-kernel block: reduction scratch, the table rows, the angle
+// weights and positions, and (FP32 two-flavour bulb kernels) the threads' state rings,
+// kStateRingDepth + 1 slots of 3 components x 2 beams per thread.
+size_t smem_bytes(int nf, size_t real_size, int max_jj, int stages, int block, bool ext = false) {
   size_t s = 32 * kNMMax * sizeof(double);
   s += (size_t)stages * max_jj * table_row_values(nf, real_size, ext) * real_size;
   s += (size_t)max_jj * real_size;                 // angle weights
   s = (s + 7) / 8 * 8 + (size_t)max_jj * sizeof(double);   // angle positions
-  return (s + 15) / 16 * 16;
+  s = (s + 15) / 16 * 16;
+  if (nf == 2 && real_size == 4 && !ext) s += (size_t)block * (kStateRingDepth + 1) * 3 * 2 * sizeof(float);
+  return s;
 }
 
 KParams make_params(xflat_t h, int n_steps, int init_only) {
@@ -575,6 +582,14 @@ KParams make_params(xflat_t h, int n_steps, int init_only) {
   p.trace = init_only ? nullptr : h->d_trace;
   p.dyn_sched = h->dyn_sched ? 1 : 0;
   p.trace_passes = (int)h->trace_passes;
+#ifdef XFLAT_BOUNDS
+  p.span[kSpanPlanes] = Span{(const char*)h->planes, h->planes_bytes};
+  p.span[kSpanEscr] = Span{(const char*)h->escr, h->escr_bytes};
+  p.span[kSpanKst] = Span{(const char*)h->kst, h->kst_bytes};
+  p.span[kSpanEtab] = Span{(const char*)h->d_etab, h->etab_bytes};
+  p.span[kSpanU] = Span{(const char*)h->d_u, h->angle_bytes};
+  p.span[kSpanDu] = Span{(const char*)h->d_du, h->angle_bytes};
+#endif
   return p;
 }
 
@@ -662,6 +677,16 @@ int read_words(xflat_t h, int& status, int& all_done) {
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   status = h->h_words[0];
   all_done = h->h_words[1];
+#ifdef XFLAT_BOUNDS
+  // checked build: name the first access the kernel found outside its allocation
+  Barrier b{};
+  CUDA_TRY(h, cudaMemcpy(&b, h->d_bar, sizeof(Barrier), cudaMemcpyDeviceToHost));
+  if (b.bounds_site) {
+    status = XFLAT_ERR_CUDA;
+    return fail(h, XFLAT_ERR_CUDA, "bounds check failed at site " + std::to_string(b.bounds_site) +
+                                       ", byte offset " + std::to_string(b.bounds_off));
+  }
+#endif
   return XFLAT_OK;
 }
 
@@ -702,21 +727,22 @@ int setup_launch_shape(xflat_t h, const xflat_config& c) {
   // 512-thread block per SM while both state buffers fit the L2 (the passes are then bound by
   // issue: the 80-register budget spills, and two co-resident blocks finish their passes at
   // different times), three 256-thread blocks once the state streams from HBM (more loads in
-  // flight); 256 threads otherwise.  (GB300, DP45, 28M beams in 64 instances: 2.07 ms per step at
-  // 256 x 3 against 2.31 ms at 512 x 1; 4M beams in one instance: 0.186 ms per one-step launch at
-  // 512 x 1 against 0.224 ms at 256 x 3.)
+  // flight); 256 threads otherwise.  (GB300, DP45, 28M beams in 64 instances with dynamic piece
+  // scheduling: 1.86 ms per step at 256 x 3 against 1.96 ms at 256 x 2 and about 2.2 ms at
+  // 512 x 1; 4M beams in one instance: 0.186 ms per one-step launch at 512 x 1 against 0.224 ms
+  // at 256 x 3.)
   const bool mixed_2f = h->nf == 2 && !h->extended && h->real_size == 4;
   int l2_bytes = 0;
   cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, h->device);
   const uint64_t state_bytes = 2ull * h->nc * h->stride * h->real_size;
   const bool resident = state_bytes <= (uint64_t)l2_bytes;
   h->block = c.block_size ? (int)c.block_size : (mixed_2f && !c.blocks_per_sm && resident ? 512 : 256);
-  const int want_bps = c.blocks_per_sm ? (int)c.blocks_per_sm : (768 / h->block);
+  const int want_bps = c.blocks_per_sm ? (int)c.blocks_per_sm : ((mixed_2f ? 512 : 768) / h->block);
   h->kernel = step_kernel_ptr(h->nf, h->precision, h->integrator, h->block, want_bps * h->block >= 768 ? 3 : 2,
                               h->extended);
   if (!h->kernel) return fail(h, XFLAT_ERR_UNSUPPORTED, "no kernel for this flavour/precision/integrator");
   const size_t smax = smem_bytes(h->nf, h->real_size, max_jj_cap(h->nf, h->real_size, h->extended),
-                                 table_stages(h->integrator), h->extended);
+                                 table_stages(h->integrator), h->block, h->extended);
   CUDA_TRY(h, cudaFuncSetAttribute(h->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
   int occ = 0;
   CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, h->kernel, h->block, smax));
@@ -732,7 +758,7 @@ int setup_launch_shape(xflat_t h, const xflat_config& c) {
   h->grid = G;
   h->dyn_sched = h->inst.size() > 1 && !h->shard;
   build_pieces(h, G);
-  h->smem = smem_bytes(h->nf, h->real_size, h->max_jj, table_stages(h->integrator), h->extended);
+  h->smem = smem_bytes(h->nf, h->real_size, h->max_jj, table_stages(h->integrator), h->block, h->extended);
   if (h->d_pieces) cudaFree(h->d_pieces);
   if (h->d_blk) cudaFree(h->d_blk);
   CUDA_TRY(h, cudaMalloc(&h->d_pieces, sizeof(Piece) * std::max<size_t>(1, h->pieces.size())));
@@ -898,16 +924,22 @@ int create_impl(const xflat_config* cfgs, uint32_t n, xflat_t* out) {
   }
   h->stride = (off + 63) / 64 * 64;
   const size_t plane_bytes = 2ull * h->nc * h->stride * h->real_size;
+  h->planes_bytes = plane_bytes;
+  h->etab_bytes = (size_t)eoff * h->real_size;
+  h->angle_bytes = sizeof(double) * aoff;
   if (cudaMalloc(&h->planes, plane_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
   // FP64 DP45: error partial (nc planes) and error scale (one plane) of the step in flight
-  if (h->integrator == XFLAT_DP45 && h->real_size == 8 &&
-      cudaMalloc(&h->escr, (size_t)(h->nc + 1) * h->stride * h->real_size) != cudaSuccess)
-    return bail(XFLAT_ERR_NOMEM);
+  if (h->integrator == XFLAT_DP45 && h->real_size == 8) {
+    h->escr_bytes = (size_t)(h->nc + 1) * h->stride * h->real_size;
+    if (cudaMalloc(&h->escr, h->escr_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
+  }
   // FP64 RK4 / DP45: the stage derivatives a step stores (k_1..k_3 of RK4, k_1..k_5 of DP45, whose
   // pass forming y5 keeps the error partial instead of k_6), then one stage state
   const int n_kst = h->real_size != 8 ? 0 : h->integrator == XFLAT_RK4 ? 3 : h->integrator == XFLAT_DP45 ? 5 : 0;
-  if (n_kst && cudaMalloc(&h->kst, (size_t)(n_kst + 1) * h->nc * h->stride * h->real_size) != cudaSuccess)
-    return bail(XFLAT_ERR_NOMEM);
+  if (n_kst) {
+    h->kst_bytes = (size_t)(n_kst + 1) * h->nc * h->stride * h->real_size;
+    if (cudaMalloc(&h->kst, h->kst_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
+  }
   if (cudaMalloc(&h->d_ic, sizeof(InstConst) * n) != cudaSuccess ||
       cudaMalloc(&h->d_dyn, sizeof(InstDyn) * n) != cudaSuccess ||
       cudaMalloc(&h->d_acc, sizeof(unsigned long long) * n * kAccWordsPerInst) != cudaSuccess ||

@@ -623,7 +623,43 @@ struct KParams {
   // block's beams and reduction, after the barrier released it, and 1 if it was the last block
   unsigned long long* trace;
   int trace_passes;
+#ifdef XFLAT_BOUNDS
+  Span span[kSpanCount];         // checked build: the allocations behind the pointers above
+#endif
 };
+
+// Checked build (-DXFLAT_BOUNDS): every state-plane, stage-plane, energy-table and angle-table
+// access of the pass body, the shared-memory row index of every beam and the piece list are tested
+// before use.  An access outside its allocation (or off the alignment of its vector type) is
+// skipped, a load yielding zeros; the first one is recorded in the barrier's bounds words and the
+// launch status becomes XFLAT_ERR_CUDA.  Without the macro every check is the constant true.
+#ifdef XFLAT_BOUNDS
+static __device__ __noinline__ void bounds_fault(const KParams& p, int site, long long off) {
+  if (atomicCAS(&p.bar->bounds_site, 0, site) == 0)
+    atomicExch(reinterpret_cast<unsigned long long*>(&p.bar->bounds_off), (unsigned long long)off);
+  atomicCAS(p.status, 0, 3 /* XFLAT_ERR_CUDA */);
+}
+__device__ __forceinline__ bool span_ok(const KParams& p, int id, const void* ptr, unsigned bytes, int site,
+                                        unsigned align = 0) {
+  const Span sp = p.span[id];
+  const char* c = static_cast<const char*>(ptr);
+  const bool ok = sp.lo != nullptr && c >= sp.lo && c + bytes <= sp.lo + sp.bytes &&
+                  (reinterpret_cast<uintptr_t>(c) % (align ? align : bytes)) == 0;
+  if (!ok) bounds_fault(p, site, sp.lo ? (long long)(c - sp.lo) : -1ll);
+  return ok;
+}
+__device__ __forceinline__ bool index_ok(const KParams& p, bool ok, int site, long long v) {
+  if (!ok) bounds_fault(p, site, v);
+  return ok;
+}
+#define XFLAT_SPAN_OK(p, id, ptr, bytes, site) ::xflat::span_ok((p), (id), (ptr), (bytes), (site))
+#define XFLAT_SPAN_OK_AL(p, id, ptr, bytes, align, site) ::xflat::span_ok((p), (id), (ptr), (bytes), (site), (align))
+#define XFLAT_INDEX_OK(p, cond, site, v) ::xflat::index_ok((p), (cond), (site), (long long)(v))
+#else
+#define XFLAT_SPAN_OK(p, id, ptr, bytes, site) true
+#define XFLAT_SPAN_OK_AL(p, id, ptr, bytes, align, site) true
+#define XFLAT_INDEX_OK(p, cond, site, v) true
+#endif
 
 // Add x (|x| < 2^63) to a 128-bit fixed-point accumulator (acc2[0]: fraction in units of 2^-64,
 // acc2[1]: signed integer part), truncating |x| below 2^-64.  The split is done on |x|, where
@@ -921,6 +957,31 @@ __device__ void serial_geometry(const KParams& p) {
 }
 
 
+// ---------------------------------------------------------------------------------------------
+// State ring of the FP32 two-flavour bulb passes.  Each thread streams its beams' state through a
+// private ring of kStateRingDepth + 1 slots in shared memory, filled by cp.async (LDGSTS)
+// kStateRingDepth vectors ahead of the one being processed: several vectors' bytes in flight per
+// thread without holding registers for them.  (Measured on GB300 against one register-held
+// prefetch vector, against 2 and 5 vectors ahead, and against a per-warp ring of 256-byte bulk
+// copies completing on mbarriers, which was slower on every launch shape.)  The slots are
+// thread-private, so the only ordering needed is the thread's own cp.async.wait_group.
+template <class Phys, typename Real>
+__host__ __device__ constexpr bool state_ring() {
+  return Phys::NC == 3 && Phys::NM == 6 && sizeof(Real) == 4;
+}
+__device__ __forceinline__ uint32_t smem_addr(const void* ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's committed groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Per-thread state vectors: two consecutive beams per load (float2 / double2), so the loaded and
 // the prefetched vectors fit the register budget; a warp still reads 256 or 512 contiguous bytes
 // per plane.
@@ -942,6 +1003,23 @@ __device__ __forceinline__ void vstore(Real* p, const Real (&v)[Vec16<Real>::N])
 #pragma unroll
   for (int i = 0; i < Vec16<Real>::N; ++i) a[i] = v[i];
   __stcg(reinterpret_cast<typename Vec16<Real>::T*>(p), t);
+}
+
+// Plane accesses of the pass body, checked in the checked build (site: where, for the record).
+template <typename Real>
+__device__ __forceinline__ void vload_at(const KParams& p, int span, const Real* ptr,
+                                         Real (&v)[Vec16<Real>::N], int site) {
+  if (XFLAT_SPAN_OK(p, span, ptr, sizeof(typename Vec16<Real>::T), site)) {
+    vload(ptr, v);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Vec16<Real>::N; ++i) v[i] = Real(0);
+  }
+}
+template <typename Real>
+__device__ __forceinline__ void vstore_at(const KParams& p, int span, Real* ptr,
+                                          const Real (&v)[Vec16<Real>::N], int site) {
+  if (XFLAT_SPAN_OK(p, span, ptr, sizeof(typename Vec16<Real>::T), site)) vstore(ptr, v);
 }
 
 // Rotation of y about Om by |Om| (right-handed): y + a Om x y + b Om x (Om x y), the Bloch form of
@@ -1703,6 +1781,27 @@ __device__ __forceinline__ void load_beam(const Real* et, int ne, int sigma, int
   bm.w = du * et[(2 + sigma) * ne + k];
 }
 
+// Checked build: a beam's energy-table entries (rows 0 .. 2 of the two-flavour tables, 0 .. 3 of
+// the three-flavour ones), its row of the shared angle tables and (stored-stage bodies) its
+// elements of the stage planes.  Always true without XFLAT_BOUNDS.
+template <class Body, int NC, typename Real>
+__device__ __forceinline__ bool beam_in_bounds(const KParams& p, const Real* et, int ne, int k, int tj,
+                                               int n_jj, const Real* kst_beam) {
+#ifdef XFLAT_BOUNDS
+  constexpr int kERowMax = NC == 3 ? 2 : 3;
+  bool ok = index_ok(p, tj >= 0 && tj < n_jj, 12, tj) && index_ok(p, k >= 0 && k < ne, 10, k) &&
+            span_ok(p, kSpanEtab, et + k, sizeof(Real), 10) &&
+            span_ok(p, kSpanEtab, et + (size_t)kERowMax * ne + k, sizeof(Real), 11);
+  if constexpr (Body::kStore)
+    ok = ok && span_ok(p, kSpanKst, kst_beam, sizeof(Real), 8) &&
+         span_ok(p, kSpanKst, kst_beam + ((size_t)(Body::kYPlanes + 1) * NC - 1) * p.plane_stride,
+                 sizeof(Real), 9);
+  return ok;
+#else
+  return true;
+#endif
+}
+
 // Stages whose table rows a pass reads (bit s set: row s needed).
 template <class Tab, int kPass, int kKind>
 __device__ __forceinline__ unsigned stages_needed() {
@@ -1722,6 +1821,8 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
   Real* dut = tab + (size_t)kTS * p.max_jj * Phys::KT;               // [max_jj]
   double* ut = reinterpret_cast<double*>(                            // [max_jj], 8-byte aligned
       (reinterpret_cast<uintptr_t>(dut + p.max_jj) + 7) & ~uintptr_t(7));
+  float* ring = reinterpret_cast<float*>(                            // [slots][NC][threads][2], 16-byte aligned
+      (reinterpret_cast<uintptr_t>(ut + p.max_jj) + 15) & ~uintptr_t(15));
   const bool mixed = sizeof(Real) == 4;
   const int slot = kKind == kInitPass ? 1 : (kKind == kStagePass ? kPass + 2 : 0);
   // Clear accumulator slots nobody reads any more (block 0, while the other blocks already work).
@@ -1764,7 +1865,11 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     } else if (pi >= b1) {
       break;
     }
+    if (!XFLAT_INDEX_OK(p, pi >= 0 && pi < p.n_pieces, 13, pi)) break;
     const Piece pc = p.pieces[pi];
+    if (!XFLAT_INDEX_OK(p, pc.inst >= 0 && pc.inst < p.n_inst && (int)pc.n_jj <= p.max_jj &&
+                               (uint64_t)pc.start + pc.len <= p.ic[pc.inst].n_beams, 14, pi))
+      continue;
     const InstConst& ic = p.ic[pc.inst];
     const InstDyn* d = p.dyn + pc.inst;
     __syncthreads();
@@ -1856,6 +1961,13 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       for (int t = threadIdx.x; t < (int)pc.n_jj; t += blockDim.x) {
         const int jj = pc.jj_lo + t;
         const int j = jj >= (int)ic.n_angle ? jj - (int)ic.n_angle : jj;
+        if (!(XFLAT_INDEX_OK(p, j >= 0 && j < (int)ic.n_angle, 15, jj) &&
+              XFLAT_SPAN_OK(p, kSpanDu, p.du_tab + ic.a_off + j, sizeof(double), 16) &&
+              XFLAT_SPAN_OK(p, kSpanU, p.u_tab + ic.a_off + j, sizeof(double), 16))) {
+          dut[t] = Real(0);
+          ut[t] = 0.0;
+          continue;
+        }
         dut[t] = (Real)p.du_tab[ic.a_off + j];
         ut[t] = p.u_tab[ic.a_off + j];
       }
@@ -1910,40 +2022,76 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
     float emax2 = 0.0f;
     const uint32_t end = pc.start + pc.len;
     const uint32_t vstep = VN * blockDim.x;
-    // two flavours: the next vector's state is loaded while this one is processed, so the L2/HBM
-    // latency of the stream overlaps the arithmetic
-    constexpr bool kPrefetch = NC == 3;
+    // FP32 two-flavour bulb passes: the state comes through the thread's ring, kStateRingDepth vectors
+    // ahead (see state_ring).  Other two-flavour passes: the next vector's state is loaded into
+    // registers while this one is processed.  Either way the L2/HBM latency of the stream overlaps
+    // the arithmetic.
+    constexpr bool kRingLoad = state_ring<Phys, Real>();
+    constexpr bool kPrefetch = NC == 3 && !kRingLoad;
     Real nxt[NC][VN];
     if (kPrefetch && pc.start + VN * threadIdx.x < end) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) vload(ysrc + (size_t)c * p.plane_stride + pc.start + VN * threadIdx.x, nxt[c]);
+      for (int c = 0; c < NC; ++c) vload_at(p, kSpanPlanes, ysrc + (size_t)c * p.plane_stride + pc.start + VN * threadIdx.x, nxt[c], 1);
+    }
+    constexpr int ring_d = kStateRingDepth;
+    constexpr uint32_t ring_slots = (uint32_t)ring_d + 1u;
+    uint32_t q_fill = 0, q_read = 0;
+    // start the copies of the vector at beam l (if it is in the piece) into the next slot; one
+    // commit group per vector, empty past the end, so the group count stays in step
+    auto ring_fill = [&](uint32_t l) {
+      if (l < end) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const Real* src = ysrc + (size_t)c * p.plane_stride + l;
+          if (XFLAT_SPAN_OK(p, kSpanPlanes, src, 2 * sizeof(Real), 1))
+            cp_async8(ring + (((size_t)q_fill * NC + c) * blockDim.x + threadIdx.x) * 2, src);
+        }
+      }
+      cp_async_commit();
+      q_fill = q_fill + 1u == ring_slots ? 0u : q_fill + 1u;
+    };
+    if constexpr (kRingLoad) {
+      for (int j = 0; j < ring_d; ++j) ring_fill(pc.start + VN * threadIdx.x + (uint32_t)j * vstep);
     }
     for (uint32_t l0 = pc.start + VN * threadIdx.x; l0 < end; l0 += vstep) {
       Real ys[NC][VN];
-      if constexpr (kPrefetch) {
+      if constexpr (kRingLoad) {
+        // the slot filled now is the one read in the previous iteration (kStateRingDepth + 1 slots)
+        ring_fill(l0 + (uint32_t)ring_d * vstep);
+        cp_async_wait_pending<ring_d>();
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const float2 t = *reinterpret_cast<const float2*>(ring + (((size_t)q_read * NC + c) * blockDim.x + threadIdx.x) * 2);
+          ys[c][0] = t.x;
+          ys[c][1] = t.y;
+        }
+        q_read = q_read + 1u == ring_slots ? 0u : q_read + 1u;
+      } else if constexpr (kPrefetch) {
 #pragma unroll
         for (int c = 0; c < NC; ++c)
 #pragma unroll
           for (int v = 0; v < VN; ++v) ys[c][v] = nxt[c][v];
         if (l0 + vstep < end) {
 #pragma unroll
-          for (int c = 0; c < NC; ++c) vload(ysrc + (size_t)c * p.plane_stride + l0 + vstep, nxt[c]);
+          for (int c = 0; c < NC; ++c) vload_at(p, kSpanPlanes, ysrc + (size_t)c * p.plane_stride + l0 + vstep, nxt[c], 2);
         }
       } else {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) vload(ysrc + (size_t)c * p.plane_stride + l0, ys[c]);
+        for (int c = 0; c < NC; ++c) vload_at(p, kSpanPlanes, ysrc + (size_t)c * p.plane_stride + l0, ys[c], 3);
       }
       Real ep[NC + 1][VN];
       if constexpr (kSplitLoad) {
 #pragma unroll
-        for (int c = 0; c <= NC; ++c) vload(escr + (size_t)c * p.plane_stride + l0, ep[c]);
+        for (int c = 0; c <= NC; ++c) vload_at(p, kSpanEscr, escr + (size_t)c * p.plane_stride + l0, ep[c], 4);
       }
       int jj = (int)fast_div(l0, ic.div_magic);
       int k = (int)l0 - jj * ne;
       bool paired = false;
       if constexpr (kPair) {
         // both beams in the same angle bin (all but the rare pair that straddles two bins)
-        if (l0 + 1 < end && k + 1 < ne) {
+        if (l0 + 1 < end && k + 1 < ne &&
+            beam_in_bounds<Body, NC, Real>(p, et, ne, k, jj - (int)pc.jj_lo, n_jj, nullptr) &&
+            beam_in_bounds<Body, NC, Real>(p, et, ne, k + 1, jj - (int)pc.jj_lo, n_jj, nullptr)) {
           paired = true;
           const int sigma = jj >= na ? 1 : 0;
           const int tj = jj - (int)pc.jj_lo;
@@ -1971,7 +2119,9 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       if (!paired) {
 #pragma unroll
         for (int v = 0; v < VN; ++v) {
-          if (l0 + v < end) {
+          if (l0 + v < end &&
+              beam_in_bounds<Body, NC, Real>(p, et, ne, k, jj - (int)pc.jj_lo, n_jj,
+                                             Body::kStore ? kst + l0 + v : nullptr)) {
             const int sigma = jj >= na ? 1 : 0;
             const int tj = jj - (int)pc.jj_lo;
             typename Phys::Beam bm;
@@ -2002,15 +2152,16 @@ __device__ void run_pass(const KParams& p, BlockShared<Real, Phys>& bs, unsigned
       }
       if constexpr (kKind == kFinalPass && !kSplitLoad) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) vstore(yout + (size_t)c * p.plane_stride + l0, ys[c]);
+        for (int c = 0; c < NC; ++c) vstore_at(p, kSpanPlanes, yout + (size_t)c * p.plane_stride + l0, ys[c], 5);
       }
       if constexpr (kSplitStore) {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) vstore(yout + (size_t)c * p.plane_stride + l0, ys[c]);
+        for (int c = 0; c < NC; ++c) vstore_at(p, kSpanPlanes, yout + (size_t)c * p.plane_stride + l0, ys[c], 6);
 #pragma unroll
-        for (int c = 0; c <= NC; ++c) vstore(escr + (size_t)c * p.plane_stride + l0, ep[c]);
+        for (int c = 0; c <= NC; ++c) vstore_at(p, kSpanEscr, escr + (size_t)c * p.plane_stride + l0, ep[c], 7);
       }
     }
+    if constexpr (kRingLoad) cp_async_wait_pending<0>();  // nothing in flight into the ring after the piece
     if constexpr (kPair) emax = fmax(emax, (Real)emax2);
     // the pass forming Y_S also checked the step's input state (non-finite: fatal)
     if constexpr (kSplitStore) {

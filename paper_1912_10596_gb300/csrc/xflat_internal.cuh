@@ -14,6 +14,7 @@
 namespace xflat {
 
 constexpr int kMaxStages = 12;      // stage slots 0..11 (Richardson-controlled CF4: 11 stages)
+constexpr int kStateRingDepth = 3;  // FP32 two-flavour bulb passes: state vectors in flight per thread
 constexpr int kNM2 = 6;             // 2 flavours: j0 (3) and j1 (3) Bloch components
 constexpr int kNM3 = 18;            // 3 flavours: j0 and j1, 9 reals each
 constexpr int kNSC2 = 8;            // stage constants: mu*j0 (3), mu*j1 (3), lambda, R^2/r^2
@@ -96,8 +97,19 @@ struct Barrier {
   // flag) takes pieces from chunk[(g >> 1) & 1]; the last block at a barrier zeroes the counter
   // of the pass that follows it before the release
   unsigned int chunk[2];
-  int pad2[27];
+  // checked build (-DXFLAT_BOUNDS): the first access found outside its allocation (site number,
+  // byte offset from the allocation's start)
+  int bounds_site;
+  long long bounds_off;
+  int pad2[24];
 };
+
+// Checked build: the allocations the step kernel's pass body reads and writes, by role.
+struct Span {
+  const char* lo;
+  unsigned long long bytes;
+};
+enum SpanId : int { kSpanPlanes = 0, kSpanEscr, kSpanKst, kSpanEtab, kSpanU, kSpanDu, kSpanCount };
 
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long globaltimer_ns() {

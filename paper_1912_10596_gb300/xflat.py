@@ -9,7 +9,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libxflat.so")
+# XFLAT_VARIANT=bounds or sanitize loads that checking build (build.build(variant=...)) instead
+_VARIANT = os.environ.get("XFLAT_VARIANT", "")
+_LIB_PATH = os.path.join(_HERE, f"libxflat_{_VARIANT}.so" if _VARIANT else "libxflat.so")
 if not os.path.exists(_LIB_PATH):
     raise ImportError(f"{_LIB_PATH} is missing: run `python -c 'import __graft_entry__ as g; g.build()'`")
 _lib = C.CDLL(_LIB_PATH)
