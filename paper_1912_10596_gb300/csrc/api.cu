@@ -459,30 +459,38 @@ void reset_dyn(xflat_t h, uint32_t i, double r0) {
 }
 
 // Cut all instances into G slices and slices into pieces; blk[b]..blk[b+1] are block b's pieces.
-// Dynamic scheduling: every instance's beams cut into pieces of about kDynChunk vector iterations
-// per thread (and at most the table's rows); blocks take them in order from a counter.
-constexpr uint32_t kDynChunk = 32;
+// Dynamic scheduling: blocks take pieces in list order from a counter.  The list holds first every
+// instance's leading beams in pieces of about kDynBig vector iterations per thread, then the last
+// kDynTailPct percent of every instance in pieces of kDynSmall iterations (each at most the table's
+// rows): the large pieces keep the per-piece set-up rare, the small ones at the end of the list let
+// the blocks finish a pass within a small piece of one another.
+constexpr uint32_t kDynBig = 64, kDynSmall = 8, kDynTailPct = 15;
 void build_dynamic_pieces(xflat_t h) {
   h->pieces.clear();
   h->blk.assign(h->grid + 1, 0);
   h->max_jj = 1;
-  const uint64_t chunk = (uint64_t)kDynChunk * 2 * h->block;
-  for (uint32_t i = 0; i < h->inst.size(); ++i) {
+  auto cut = [&](uint32_t i, uint64_t a0, uint64_t a1, uint32_t iters) {
     const HostInst& I = h->inst[i];
     const uint32_t ne = I.cfg.n_energy;
     const uint64_t rows_cap = std::max<uint64_t>(kAlignBeams, ((uint64_t)(max_jj_cap(h->nf, h->real_size, h->extended) - 1) * ne) / kAlignBeams * kAlignBeams);
-    const uint64_t len = std::min<uint64_t>(chunk, rows_cap);
-    for (uint64_t a = 0; a < I.n_beams; a += len) {
+    const uint64_t len = std::min<uint64_t>((uint64_t)iters * 2 * h->block, rows_cap);
+    for (uint64_t a = a0; a < a1; a += len) {
       Piece p{};
       p.inst = (int)i;
       p.start = (uint32_t)a;
-      p.len = (uint32_t)std::min<uint64_t>(len, I.n_beams - a);
+      p.len = (uint32_t)std::min<uint64_t>(len, a1 - a);
       p.jj_lo = p.start / ne;
       p.n_jj = (p.start + p.len - 1) / ne - p.jj_lo + 1;
       h->max_jj = std::max<int>(h->max_jj, (int)p.n_jj);
       h->pieces.push_back(p);
     }
+  };
+  std::vector<uint64_t> split(h->inst.size());
+  for (uint32_t i = 0; i < h->inst.size(); ++i) {
+    split[i] = ((uint64_t)h->inst[i].n_beams * (100 - kDynTailPct) / 100) / kAlignBeams * kAlignBeams;
+    cut(i, 0, split[i], kDynBig);
   }
+  for (uint32_t i = 0; i < h->inst.size(); ++i) cut(i, split[i], h->inst[i].n_beams, kDynSmall);
 }
 
 void build_pieces(xflat_t h, int G) {
