@@ -132,7 +132,8 @@ typedef struct {
   double R_km;                /* neutrino-sphere radius R                                          */
   double E_min_MeV, E_max_MeV;/* energy range, bins of equal width, midpoints                      */
   double dm2_eV2[2];          /* 2 flavours: dm2[0]; 3 flavours: dm2_21, dm2_31 (signed)          */
-  double theta[3];            /* 2 flavours: theta[0] = theta_v; 3 flavours: theta12, 13, 23 (rad) */
+  double theta[3];            /* 2 flavours: theta[0] = theta_v; 3 flavours: theta12, 13, 23 (rad),
+                                 U = R23 R13 R12 with a zero CP phase (real mixing)              */
   double rtol, atol;          /* DP45 error control (see xflat_evolve)                             */
   double h0_km;               /* DP45 first trial step                                             */
   double h_min_km, h_max_km;  /* DP45 step bounds (h_max_km <= 0: unbounded)                       */
