@@ -381,6 +381,12 @@ const char* xflat_last_error(xflat_t h);
  * call returns XFLAT_ERR_TIMEOUT with the context intact.  0 restores normal operation. */
 int xflat_debug_barrier_extra(xflat_t h, uint32_t extra);
 
+/* Test hook for the cleanup paths: the nth device or pinned-host allocation the library makes after
+ * this call fails as if memory were exhausted (process-wide, once); 0 disarms.  The call that made
+ * the allocation returns XFLAT_ERR_NOMEM or XFLAT_ERR_CUDA after freeing what it had allocated; a
+ * handle that existed before stays usable.  Returns XFLAT_OK. */
+int xflat_debug_fail_alloc(uint32_t nth);
+
 /* Pass trace (profiling aid).  host_out == NULL: arm tracing of the first n_passes passes of every
  * following step launch (n_passes = 0 disarms; the handle allocates n_passes x grid x 4 u64 of
  * device memory).  host_out != NULL: synchronise and copy the trace out: for pass i and block b,

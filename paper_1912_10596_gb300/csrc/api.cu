@@ -1,5 +1,6 @@
 // C ABI of the bulb-model solver: argument checks, tables, memory, launches (see include/xflat.h).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,9 +14,47 @@
 #include "xflat_internal.cuh"
 #include "step_kernel.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace xflat;
 
 namespace {
+
+// ---- tracing and allocation-failure injection ---------------------------------------------------
+// Every exported call is one NVTX range named after the call (visible in any NVTX-aware profiler;
+// a check of one pointer when none is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+#define XFLAT_TRACE() NvtxRange xflat_trace_range_(__func__)
+
+// Allocation-failure injection for tests of the cleanup paths: after xflat_debug_fail_alloc(n),
+// the n-th device or pinned-host allocation the library makes fails as if memory were exhausted
+// (process-wide, once; 0 disarms).
+std::atomic<long> g_fail_alloc{0};
+bool injected_failure() {
+  long v = g_fail_alloc.load();
+  while (v > 0)
+    if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 1;
+  return false;
+}
+template <class T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+cudaError_t host_alloc(T** p, size_t bytes) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(reinterpret_cast<void**>(p), bytes);
+}
 
 // ---- physical constants (CODATA 2018 / SI 2019) ------------------------------------------------
 constexpr double kGF = 1.1663787e-5;                       // G_F / (hbar c)^3, GeV^-2
@@ -769,8 +808,10 @@ int setup_launch_shape(xflat_t h, const xflat_config& c) {
   h->smem = smem_bytes(h->nf, h->real_size, h->max_jj, table_stages(h->integrator), h->block, h->extended);
   if (h->d_pieces) cudaFree(h->d_pieces);
   if (h->d_blk) cudaFree(h->d_blk);
-  CUDA_TRY(h, cudaMalloc(&h->d_pieces, sizeof(Piece) * std::max<size_t>(1, h->pieces.size())));
-  CUDA_TRY(h, cudaMalloc(&h->d_blk, sizeof(int) * h->blk.size()));
+  h->d_pieces = nullptr;
+  h->d_blk = nullptr;
+  CUDA_TRY(h, dev_alloc(&h->d_pieces, sizeof(Piece) * std::max<size_t>(1, h->pieces.size())));
+  CUDA_TRY(h, dev_alloc(&h->d_blk, sizeof(int) * h->blk.size()));
   CUDA_TRY(h, cudaMemcpy(h->d_pieces, h->pieces.data(), sizeof(Piece) * h->pieces.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(h, cudaMemcpy(h->d_blk, h->blk.data(), sizeof(int) * h->blk.size(), cudaMemcpyHostToDevice));
   return XFLAT_OK;
@@ -781,7 +822,7 @@ int ensure_stage(xflat_t h, size_t bytes) {
   if (h->d_stage) cudaFree(h->d_stage);
   h->d_stage = nullptr;
   h->stage_bytes = 0;
-  CUDA_TRY(h, cudaMalloc(&h->d_stage, bytes));
+  CUDA_TRY(h, dev_alloc(&h->d_stage, bytes));
   h->stage_bytes = bytes;
   return XFLAT_OK;
 }
@@ -935,30 +976,30 @@ int create_impl(const xflat_config* cfgs, uint32_t n, xflat_t* out) {
   h->planes_bytes = plane_bytes;
   h->etab_bytes = (size_t)eoff * h->real_size;
   h->angle_bytes = sizeof(double) * aoff;
-  if (cudaMalloc(&h->planes, plane_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
+  if (dev_alloc(&h->planes, plane_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
   // FP64 DP45: error partial (nc planes) and error scale (one plane) of the step in flight
   if (h->integrator == XFLAT_DP45 && h->real_size == 8) {
     h->escr_bytes = (size_t)(h->nc + 1) * h->stride * h->real_size;
-    if (cudaMalloc(&h->escr, h->escr_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
+    if (dev_alloc(&h->escr, h->escr_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
   }
   // FP64 RK4 / DP45: the stage derivatives a step stores (k_1..k_3 of RK4, k_1..k_5 of DP45, whose
   // pass forming y5 keeps the error partial instead of k_6), then one stage state
   const int n_kst = h->real_size != 8 ? 0 : h->integrator == XFLAT_RK4 ? 3 : h->integrator == XFLAT_DP45 ? 5 : 0;
   if (n_kst) {
     h->kst_bytes = (size_t)(n_kst + 1) * h->nc * h->stride * h->real_size;
-    if (cudaMalloc(&h->kst, h->kst_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
+    if (dev_alloc(&h->kst, h->kst_bytes) != cudaSuccess) return bail(XFLAT_ERR_NOMEM);
   }
-  if (cudaMalloc(&h->d_ic, sizeof(InstConst) * n) != cudaSuccess ||
-      cudaMalloc(&h->d_dyn, sizeof(InstDyn) * n) != cudaSuccess ||
-      cudaMalloc(&h->d_acc, sizeof(unsigned long long) * n * kAccWordsPerInst) != cudaSuccess ||
-      cudaMalloc(&h->d_errmax, sizeof(unsigned long long) * n) != cudaSuccess ||
-      cudaMalloc(&h->d_nonfinite, sizeof(int) * n) != cudaSuccess ||
-      cudaMalloc(&h->d_etab, (size_t)eoff * h->real_size) != cudaSuccess ||
-      cudaMalloc(&h->d_u, sizeof(double) * aoff) != cudaSuccess ||
-      cudaMalloc(&h->d_du, sizeof(double) * aoff) != cudaSuccess ||
-      cudaMalloc(&h->d_bar, sizeof(Barrier)) != cudaSuccess ||
-      cudaMalloc(&h->d_words, 2 * sizeof(int)) != cudaSuccess ||
-      cudaMallocHost(&h->h_words, 2 * sizeof(int)) != cudaSuccess)
+  if (dev_alloc(&h->d_ic, sizeof(InstConst) * n) != cudaSuccess ||
+      dev_alloc(&h->d_dyn, sizeof(InstDyn) * n) != cudaSuccess ||
+      dev_alloc(&h->d_acc, sizeof(unsigned long long) * n * kAccWordsPerInst) != cudaSuccess ||
+      dev_alloc(&h->d_errmax, sizeof(unsigned long long) * n) != cudaSuccess ||
+      dev_alloc(&h->d_nonfinite, sizeof(int) * n) != cudaSuccess ||
+      dev_alloc(&h->d_etab, (size_t)eoff * h->real_size) != cudaSuccess ||
+      dev_alloc(&h->d_u, sizeof(double) * aoff) != cudaSuccess ||
+      dev_alloc(&h->d_du, sizeof(double) * aoff) != cudaSuccess ||
+      dev_alloc(&h->d_bar, sizeof(Barrier)) != cudaSuccess ||
+      dev_alloc(&h->d_words, 2 * sizeof(int)) != cudaSuccess ||
+      host_alloc(&h->h_words, 2 * sizeof(int)) != cudaSuccess)
     return bail(XFLAT_ERR_NOMEM);
   cudaMemset(h->d_etab, 0, (size_t)eoff * h->real_size);
   h->ic.assign(n, InstConst{});
@@ -987,6 +1028,7 @@ int create_impl(const xflat_config* cfgs, uint32_t n, xflat_t* out) {
 extern "C" {
 
 int xflat_default_config(xflat_config* c) {
+  XFLAT_TRACE();
   if (!c) return XFLAT_ERR_INVAL;
   std::memset(c, 0, sizeof(*c));
   c->abi_version = XFLAT_ABI_VERSION;
@@ -1014,13 +1056,16 @@ int xflat_default_config(xflat_config* c) {
   return XFLAT_OK;
 }
 
-int xflat_create(const xflat_config* cfg, xflat_t* out) { return create_impl(cfg, 1, out); }
+int xflat_create(const xflat_config* cfg, xflat_t* out) {
+  XFLAT_TRACE(); return create_impl(cfg, 1, out); }
 
 int xflat_create_batch(const xflat_config* cfgs, uint32_t n_inst, xflat_t* out) {
+  XFLAT_TRACE();
   return create_impl(cfgs, n_inst, out);
 }
 
 int xflat_destroy(xflat_t h) {
+  XFLAT_TRACE();
   if (!h) return XFLAT_OK;
   if (h->stream || true) cudaStreamSynchronize(h->stream);
   drop_graph(h);
@@ -1043,13 +1088,19 @@ int upload_matter_tables(xflat_t h) {
     off[i] = all.size();
     all.insert(all.end(), h->inst[i].mtab.begin(), h->inst[i].mtab.end());
   }
-  if (h->d_mtab) cudaFree(h->d_mtab);
-  h->d_mtab = nullptr;
+  // the new array is filled before the old one is released: a failure leaves the device copy and
+  // the instance constants as they were
+  double* fresh = nullptr;
   if (!all.empty()) {
-    if (cudaMalloc(&h->d_mtab, all.size() * sizeof(double)) != cudaSuccess)
+    if (dev_alloc(&fresh, all.size() * sizeof(double)) != cudaSuccess)
       return fail(h, XFLAT_ERR_NOMEM, "matter table");
-    CUDA_TRY(h, cudaMemcpy(h->d_mtab, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (cudaMemcpy(fresh, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(fresh);
+      return fail(h, XFLAT_ERR_CUDA, "matter table upload");
+    }
   }
+  if (h->d_mtab) cudaFree(h->d_mtab);
+  h->d_mtab = fresh;
   for (size_t i = 0; i < h->inst.size(); ++i) {
     h->ic[i].mt_n = (int32_t)(h->inst[i].mtab.size() / 3);
     h->ic[i].mtab = h->ic[i].mt_n ? h->d_mtab + off[i] : nullptr;
@@ -1059,6 +1110,7 @@ int upload_matter_tables(xflat_t h) {
 
 int xflat_set_matter_table(xflat_t h, uint32_t inst, const double* r_km, const double* lambda_kmi,
                            uint32_t n) {
+  XFLAT_TRACE();
   if (!h) return XFLAT_ERR_INVAL;
   if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
   HostInst& I = h->inst[inst];
@@ -1075,10 +1127,14 @@ int xflat_set_matter_table(xflat_t h, uint32_t inst, const double* r_km, const d
     t[3 * i + 1] = lambda_kmi[i];
     t[3 * i + 2] = i + 1 < n ? std::log(lambda_kmi[i + 1] / lambda_kmi[i]) / std::log(r_km[i + 1] / r_km[i]) : 0.0;
   }
-  I.mtab = t;
   int rc;
   if ((rc = download_dyn(h))) return rc;
-  if ((rc = upload_matter_tables(h))) return rc;
+  std::vector<double> previous = std::move(I.mtab);
+  I.mtab = std::move(t);
+  if ((rc = upload_matter_tables(h))) {
+    I.mtab = std::move(previous);           // the device still holds the previous tables
+    return rc;
+  }
   // the stage strengths of the current step were computed with the previous profile
   h->moments_valid = false;
   return XFLAT_OK;
@@ -1086,6 +1142,7 @@ int xflat_set_matter_table(xflat_t h, uint32_t inst, const double* r_km, const d
 
 int xflat_set_spectra_inst(xflat_t h, uint32_t inst, const double* nnu, const double* u_bins,
                            const double* u_weights) {
+  XFLAT_TRACE();
   if (!h) return XFLAT_ERR_INVAL;
   if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
   if (!nnu) return fail(h, XFLAT_ERR_INVAL, "nnu is NULL");
@@ -1132,10 +1189,12 @@ int xflat_set_spectra_inst(xflat_t h, uint32_t inst, const double* nnu, const do
 }
 
 int xflat_set_spectra(xflat_t h, const double* nnu, const double* u_bins, const double* u_weights) {
+  XFLAT_TRACE();
   return xflat_set_spectra_inst(h, 0, nnu, u_bins, u_weights);
 }
 
 int xflat_reset(xflat_t h, double r0_km) {
+  XFLAT_TRACE();
   if (!h) return XFLAT_ERR_INVAL;
   if (!is_fin(r0_km)) return fail(h, XFLAT_ERR_INVAL, "r0 not finite");
   int rc;
@@ -1153,11 +1212,13 @@ int xflat_reset(xflat_t h, double r0_km) {
 }
 
 int xflat_evolve_batch(xflat_t h, const double* r1) {
+  XFLAT_TRACE();
   if (!h || !r1) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
   return do_evolve(h, r1, true, 0, nullptr);
 }
 
 int xflat_evolve(xflat_t h, double r0_km, double r1_km) {
+  XFLAT_TRACE();
   if (!h) return XFLAT_ERR_INVAL;
   int rc;
   if ((rc = download_dyn(h))) return rc;
@@ -1170,12 +1231,14 @@ int xflat_evolve(xflat_t h, double r0_km, double r1_km) {
 }
 
 int xflat_advance(xflat_t h, const double* r1, uint32_t max_steps, int* done_out) {
+  XFLAT_TRACE();
   if (!h) return XFLAT_ERR_INVAL;
   if (max_steps == 0) return fail(h, XFLAT_ERR_INVAL, "max_steps must be >= 1");
   return do_evolve(h, r1, false, max_steps, done_out);
 }
 
 int xflat_advance_graph(xflat_t h, uint32_t n_launches, uint32_t max_steps, int* done_out) {
+  XFLAT_TRACE();
   if (!h) return XFLAT_ERR_INVAL;
   if (n_launches == 0 || max_steps == 0) return fail(h, XFLAT_ERR_INVAL, "n_launches and max_steps must be >= 1");
   if (!(h->advancing && h->moments_valid))
@@ -1190,6 +1253,7 @@ int xflat_advance_graph(xflat_t h, uint32_t n_launches, uint32_t max_steps, int*
 }
 
 int xflat_moments_inst(xflat_t h, uint32_t inst, double* J0, double* J1) {
+  XFLAT_TRACE();
   if (!h || !J0 || !J1) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
   if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
   if (!h->inst[inst].spectra) return fail(h, XFLAT_ERR_STATE, "set_spectra first");
@@ -1227,9 +1291,11 @@ int xflat_moments_inst(xflat_t h, uint32_t inst, double* J0, double* J1) {
   return XFLAT_OK;
 }
 
-int xflat_moments(xflat_t h, double* J0, double* J1) { return xflat_moments_inst(h, 0, J0, J1); }
+int xflat_moments(xflat_t h, double* J0, double* J1) {
+  XFLAT_TRACE(); return xflat_moments_inst(h, 0, J0, J1); }
 
 int xflat_moments_phi(xflat_t h, uint32_t inst, double* Jc, double* Js) {
+  XFLAT_TRACE();
   if (!h || !Jc || !Js) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
   if (!h->extended) return fail(h, XFLAT_ERR_UNSUPPORTED, "azimuthal moments need the extended bulb model");
   if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
@@ -1251,6 +1317,7 @@ int xflat_moments_phi(xflat_t h, uint32_t inst, double* Jc, double* Js) {
 }
 
 int xflat_get_rho_inst(xflat_t h, uint32_t inst, void* dst, int dst_is_device, int layout) {
+  XFLAT_TRACE();
   if (!h || !dst) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
   if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
   if (layout != XFLAT_LAYOUT_MATRIX && layout != XFLAT_LAYOUT_NATIVE) return fail(h, XFLAT_ERR_INVAL, "bad layout");
@@ -1275,10 +1342,12 @@ int xflat_get_rho_inst(xflat_t h, uint32_t inst, void* dst, int dst_is_device, i
 }
 
 int xflat_get_rho(xflat_t h, void* dst, int dst_is_device, int layout) {
+  XFLAT_TRACE();
   return xflat_get_rho_inst(h, 0, dst, dst_is_device, layout);
 }
 
 int xflat_set_rho_inst(xflat_t h, uint32_t inst, const void* src, int src_is_device, int layout, double r_km) {
+  XFLAT_TRACE();
   if (!h || !src) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
   if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
   if (layout != XFLAT_LAYOUT_MATRIX && layout != XFLAT_LAYOUT_NATIVE) return fail(h, XFLAT_ERR_INVAL, "bad layout");
@@ -1311,10 +1380,12 @@ int xflat_set_rho_inst(xflat_t h, uint32_t inst, const void* src, int src_is_dev
 }
 
 int xflat_set_rho(xflat_t h, const void* src, int src_is_device, int layout, double r_km) {
+  XFLAT_TRACE();
   return xflat_set_rho_inst(h, 0, src, src_is_device, layout, r_km);
 }
 
 int xflat_pee_inst(xflat_t h, uint32_t inst, double* pee_per_beam, double* pee_mean) {
+  XFLAT_TRACE();
   if (!h) return XFLAT_ERR_INVAL;
   if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
   int rc;
@@ -1346,10 +1417,12 @@ int xflat_pee_inst(xflat_t h, uint32_t inst, double* pee_per_beam, double* pee_m
 }
 
 int xflat_pee(xflat_t h, double* pee_per_beam, double* pee_mean) {
+  XFLAT_TRACE();
   return xflat_pee_inst(h, 0, pee_per_beam, pee_mean);
 }
 
 int xflat_flux_spectra(xflat_t h, uint32_t inst, double* flux) {
+  XFLAT_TRACE();
   if (!h || !flux) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
   if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
   if (!h->inst[inst].spectra) return fail(h, XFLAT_ERR_STATE, "set_spectra first");
@@ -1374,6 +1447,7 @@ int xflat_flux_spectra(xflat_t h, uint32_t inst, double* flux) {
 }
 
 int xflat_get_stats_inst(xflat_t h, uint32_t inst, xflat_stats* out) {
+  XFLAT_TRACE();
   if (!h || !out) return fail(h, XFLAT_ERR_INVAL, "NULL argument");
   if (inst >= h->inst.size()) return fail(h, XFLAT_ERR_INVAL, "instance index out of range");
   int rc;
@@ -1398,10 +1472,12 @@ int xflat_get_stats_inst(xflat_t h, uint32_t inst, xflat_stats* out) {
   return XFLAT_OK;
 }
 
-int xflat_get_stats(xflat_t h, xflat_stats* out) { return xflat_get_stats_inst(h, 0, out); }
+int xflat_get_stats(xflat_t h, xflat_stats* out) {
+  XFLAT_TRACE(); return xflat_get_stats_inst(h, 0, out); }
 
 int xflat_adjoint(xflat_t h, double r0_km, double r1_km, uint32_t n_steps, uint32_t checkpoint_every,
                   double* dJ_dN, double* dJ_dtheta, double* J_out) {
+  XFLAT_TRACE();
   if (!h) return XFLAT_ERR_INVAL;
   if (h->nf != 2 || h->inst.size() != 1 || h->extended || h->inst[0].cfg.geometry != XFLAT_GEOMETRY_BULB ||
       h->inst[0].cfg.matter_kind == XFLAT_MATTER_TABLE)
@@ -1439,8 +1515,8 @@ int xflat_adjoint(xflat_t h, double r0_km, double r1_km, uint32_t n_steps, uint3
   double* base = nullptr;
   Barrier* bar = nullptr;
   int* status = nullptr;
-  if (cudaMalloc(&base, words * sizeof(double)) != cudaSuccess) return fail(h, XFLAT_ERR_NOMEM, "adjoint buffers");
-  if (cudaMalloc(&bar, sizeof(Barrier)) != cudaSuccess || cudaMalloc(&status, sizeof(int)) != cudaSuccess) {
+  if (dev_alloc(&base, words * sizeof(double)) != cudaSuccess) return fail(h, XFLAT_ERR_NOMEM, "adjoint buffers");
+  if (dev_alloc(&bar, sizeof(Barrier)) != cudaSuccess || dev_alloc(&status, sizeof(int)) != cudaSuccess) {
     cudaFree(base);
     if (bar) cudaFree(bar);
     return fail(h, XFLAT_ERR_NOMEM, "adjoint barrier");
@@ -1553,6 +1629,7 @@ int xflat_adjoint(xflat_t h, double r0_km, double r1_km, uint32_t n_steps, uint3
 // ---- beam shards: one problem over several GPUs (Sec. 3.3's decomposition of the angle bins and
 // the sum of the Eq. F integrals over ranks at every evaluation) ---------------------------------
 int xflat_create_shard(const xflat_config* cfg, uint32_t beam_lo, uint32_t beam_hi, xflat_t* out) {
+  XFLAT_TRACE();
   if (!cfg || !out) return XFLAT_ERR_INVAL;
   xflat_t h = nullptr;
   int rc = create_impl(cfg, 1, &h);
@@ -1576,6 +1653,7 @@ int xflat_create_shard(const xflat_config* cfg, uint32_t beam_lo, uint32_t beam_
 }
 
 int xflat_shard_info(xflat_t h, uint32_t* passes_per_step, uint32_t* n_words) {
+  XFLAT_TRACE();
   if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
   const int it = h->integrator;
   const uint32_t passes = it == XFLAT_DP45 ? 7 : it == XFLAT_EXP_MIDPOINT ? 2 : it == XFLAT_LIE_ADAPTIVE ? 11 : 4;
@@ -1586,6 +1664,7 @@ int xflat_shard_info(xflat_t h, uint32_t* passes_per_step, uint32_t* n_words) {
 }
 
 int xflat_shard_begin(xflat_t h, double r1_km) {
+  XFLAT_TRACE();
   if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
   bool any = false, changed = false;
   int rc;
@@ -1598,6 +1677,7 @@ int xflat_shard_begin(xflat_t h, double r1_km) {
 }
 
 int xflat_shard_pass(xflat_t h, int32_t pass) {
+  XFLAT_TRACE();
   if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
   uint32_t passes = 0;
   xflat_shard_info(h, &passes, nullptr);
@@ -1618,6 +1698,7 @@ int shard_slot(xflat_t h) {
 }
 
 int xflat_shard_partials(xflat_t h, int64_t* words) {
+  XFLAT_TRACE();
   if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
   if (!words) return fail(h, XFLAT_ERR_INVAL, "words is NULL");
   if (h->shard_last < -1) return fail(h, XFLAT_ERR_STATE, "no pass launched");
@@ -1648,6 +1729,7 @@ int xflat_shard_partials(xflat_t h, int64_t* words) {
 }
 
 int xflat_shard_set_totals(xflat_t h, const int64_t* words) {
+  XFLAT_TRACE();
   if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
   if (!words) return fail(h, XFLAT_ERR_INVAL, "words is NULL");
   if (h->shard_last < -1) return fail(h, XFLAT_ERR_STATE, "no pass launched");
@@ -1674,6 +1756,7 @@ int xflat_shard_set_totals(xflat_t h, const int64_t* words) {
 }
 
 int xflat_shard_serial(xflat_t h, int32_t after_moment_pass, int* done_out) {
+  XFLAT_TRACE();
   if (!h || !h->shard) return h ? fail(h, XFLAT_ERR_STATE, "not a beam-shard handle") : XFLAT_ERR_INVAL;
   uint32_t passes = 0;
   xflat_shard_info(h, &passes, nullptr);
@@ -1710,13 +1793,21 @@ const char* xflat_status_string(int s) {
 
 const char* xflat_last_error(xflat_t h) { return h ? h->err.c_str() : "NULL handle"; }
 
+int xflat_debug_fail_alloc(uint32_t nth) {
+  XFLAT_TRACE();
+  g_fail_alloc.store((long)nth);
+  return XFLAT_OK;
+}
+
 int xflat_debug_barrier_extra(xflat_t h, uint32_t extra) {
+  XFLAT_TRACE();
   if (!h) return XFLAT_ERR_INVAL;
   h->debug_extra = extra;
   return XFLAT_OK;
 }
 
 int xflat_debug_trace(xflat_t h, uint32_t n_passes, uint64_t* host_out, uint32_t* grid_out) {
+  XFLAT_TRACE();
   if (!h) return XFLAT_ERR_INVAL;
   if (grid_out) *grid_out = (uint32_t)h->grid;
   if (host_out) {
@@ -1733,7 +1824,7 @@ int xflat_debug_trace(xflat_t h, uint32_t n_passes, uint64_t* host_out, uint32_t
   }
   if (n_passes == 0) return XFLAT_OK;
   const size_t bytes = (size_t)n_passes * h->grid * 4 * 8;
-  CUDA_TRY(h, cudaMalloc(&h->d_trace, bytes));
+  CUDA_TRY(h, dev_alloc(&h->d_trace, bytes));
   CUDA_TRY(h, cudaMemset(h->d_trace, 0, bytes));
   h->trace_passes = n_passes;
   return XFLAT_OK;

@@ -89,6 +89,7 @@ _SIGS = {
     "xflat_get_stats_inst": (_H, C.c_uint32, C.POINTER(xflat_stats)),
     "xflat_adjoint": (_H, C.c_double, C.c_double, C.c_uint32, C.c_uint32, _P, _P, _P),
     "xflat_debug_barrier_extra": (_H, C.c_uint32),
+    "xflat_debug_fail_alloc": (C.c_uint32,),
     "xflat_moments_2f_noalloc": (_P, C.c_uint32, C.c_uint32, _P, _P, _P, C.c_double, C.c_double,
                                  _P, _P),
     "xflat_debug_trace": (_H, C.c_uint32, _P, C.POINTER(C.c_uint32)),
