@@ -37,6 +37,23 @@ L2_BYTES = 129 * 1024 * 1024
 STEP_TRAFFIC = {"bytes_per_launch": 54799104 + 178418176, "steps_per_launch": 8,
                 "code_sha256": "85bf3e2f915848f738f63cb341223ed7621d79945e0aa0656c60c80a3cafa363"}
 KERNEL_SOURCES = ["step_kernel.cuh", "xflat_internal.cuh", "kernels_2f.cu"]
+# Warp instructions of one radial step of the same kernel code (smsp__inst_executed.sum of one ncu
+# capture of a one-step launch, which also carries the launch's first set-up, so a step inside a
+# longer launch issues a little less): with the step time and the sampled SM clock it gives the
+# kernel's place under its instruction-issue ceiling (4 warp instructions per clock per SM).
+STEP_INSTRUCTIONS = {"warp_inst_per_step": 132210830, "code_sha256": STEP_TRAFFIC["code_sha256"]}
+
+
+def issue_roofline(ms_per_step, sm_mhz, n_sm):
+    """Issue-rate roofline of the step kernel, or None when the recorded count belongs to other code."""
+    if kernel_code_hash() != STEP_INSTRUCTIONS["code_sha256"] or not sm_mhz:
+        return None
+    achieved = STEP_INSTRUCTIONS["warp_inst_per_step"] / (ms_per_step * 1e-3)
+    peak = 4.0 * n_sm * sm_mhz * 1e6
+    return {"achieved": achieved, "peak": peak, "unit": "warp-inst/s", "frac": achieved / peak,
+            "warp_inst_per_step": STEP_INSTRUCTIONS["warp_inst_per_step"],
+            "note": "ncu warp-instruction count of a one-step launch of this kernel code; peak = 4 per clock "
+                    "per SM at the median sampled SM clock"}
 
 
 def kernel_code_hash():
@@ -716,7 +733,9 @@ def main():
                          "frac": achieved / hbm, "traffic": step_traffic(spl),
                          "note": f"{BYTES_PER_BEAM_STAGE[('mixed', 'dp45')]} algorithmic B per beam-stage "
                                  f"({BYTES_PER_BEAM_STAGE[('mixed', 'dp45')] * bsu * spl / 1e9:.2f} GB per {spl}-step launch); "
-                                 f"traffic = DRAM bytes per {spl}-step launch; peak {peak_kind}"},
+                                 f"traffic = DRAM bytes per {spl}-step launch; peak {peak_kind}",
+                         "issue": issue_roofline(t_ms / args.steps, (clocks or {}).get("sm_mhz"),
+                                                 torch.cuda.get_device_properties(0).multi_processor_count)},
             "accepted_value": value * acc_frac,
             "repeats": rep_main,
             "clocks": clocks,

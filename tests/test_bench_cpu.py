@@ -63,3 +63,14 @@ def test_kernel_code_hash_ignores_comments_only(tmp_path):
         assert bench.kernel_code_hash() != h0
     finally:
         bench.ROOT = saved
+
+
+def test_issue_roofline_uses_the_recorded_instruction_count():
+    """The issue-rate figure beside the HBM fraction: the recorded warp instructions per step over
+    the step time, against 4 warp instructions per clock per SM; none without a clock reading."""
+    r = bench.issue_roofline(0.25, 2000.0, 152)
+    assert r is not None
+    n = bench.STEP_INSTRUCTIONS["warp_inst_per_step"]
+    assert abs(r["frac"] - n / 0.25e-3 / (4 * 152 * 2000e6)) < 1e-12
+    assert bench.issue_roofline(0.25, None, 152) is None
+    assert bench.STEP_INSTRUCTIONS["code_sha256"] == bench.kernel_code_hash()
