@@ -68,13 +68,15 @@ enum xflat_integrator {
   XFLAT_RK4 = 0,              /* classical 4-stage RK on d(rho)/dr = -i[H,rho]/cos(theta), fixed step */
   XFLAT_DP45 = 1,             /* Dormand-Prince 5(4), FSAL, adaptive (error control below)        */
   XFLAT_LIE_RK4 = 2,          /* commutator-free Lie RK4 whose every update is an exact propagator
-                                 exp(-i H dl) of Eq. U (two flavours only), fixed step              */
+                                 exp(-i H dl) of Eq. U (two flavours: the closed form; three: by
+                                 the eigen-decomposition of the 3 x 3 generator), fixed step      */
   XFLAT_EXP_MIDPOINT = 3,     /* exponential midpoint rule (Lie-group Runge-Kutta-Munthe-Kaas method
                                  with Runge's midpoint tableau; Sec. 3.4's exact propagator of Eq. U
                                  with a mid-point scheme): y' = exp(-i H(r+h/2, y_half) dl) applied
                                  to y, y_half from an exponential half step; the exponential Euler
                                  step exp(-i H(r, y) dl) is the embedded first-order estimate
-                                 (error control as DP45 with the factor 0.9 Err^-1/2); two flavours */
+                                 (error control as DP45 with the factor 0.9 Err^-1/2); two and
+                                 three flavours                                                   */
   XFLAT_LIE_ADAPTIVE = 4      /* adaptive exact propagators: the commutator-free Lie RK4 of
                                  XFLAT_LIE_RK4 with Richardson step-size control -- each attempt
                                  takes one step of h and two of h/2 from the same state, keeps the
@@ -83,7 +85,7 @@ enum xflat_integrator {
                                  Every update is an exact propagator of Eq. U, so the step is set by
                                  how fast the generator changes, not by its size (no explicit
                                  stability limit near R).  11 passes (stage evaluations) per step;
-                                 two flavours, bulb model (n_phi <= 1)                               */
+                                 two and three flavours, bulb model (n_phi <= 1)                    */
 };
 enum xflat_matter {
   XFLAT_MATTER_NONE = 0,

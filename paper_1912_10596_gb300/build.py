@@ -23,8 +23,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxflat.so")
 STAMP = LIB + ".sha256"      # fingerprint of the inputs the present libxflat.so was built from
-SOURCES = ["api.cu", "kernels_2f.cu", "kernels_lie.cu", "kernels_2e.cu", "kernels_3f.cu", "adjoint_2f.cu",
-           "noalloc.cu"]
+SOURCES = ["api.cu", "kernels_2f.cu", "kernels_lie.cu", "kernels_2e.cu", "kernels_3f.cu", "kernels_3f_lie.cu",
+           "adjoint_2f.cu", "noalloc.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-diag-suppress", "128",
               "-Xptxas", "-v"]

@@ -181,10 +181,6 @@ int check_config(const xflat_config& c, std::string& why) {
   if (nb * (uint64_t)c.n_energy >= (1ull << 40)) { why = "n_beams * n_energy must be < 2^40"; return XFLAT_ERR_INVAL; }
   if (c.precision > 1) { why = "precision must be FP64 or MIXED"; return XFLAT_ERR_INVAL; }
   if (c.integrator > 4) { why = "unknown integrator"; return XFLAT_ERR_INVAL; }
-  if ((c.integrator == XFLAT_LIE_RK4 || c.integrator == XFLAT_EXP_MIDPOINT || c.integrator == XFLAT_LIE_ADAPTIVE) &&
-      c.n_flavor != 2) {
-    why = "the exponential integrators are two-flavour only"; return XFLAT_ERR_UNSUPPORTED;
-  }
   if (c.integrator == XFLAT_LIE_ADAPTIVE && c.n_phi >= 2) {
     why = "the adaptive Lie integrator is built for the bulb model only"; return XFLAT_ERR_UNSUPPORTED;
   }

@@ -10,6 +10,8 @@ const void* step_kernel_ptr(int n_flavor, int precision, int integrator, int blo
                             bool extended = false);
 // The adaptive Lie integrator's step kernels (two flavours, bulb model; kernels_lie.cu).
 const void* step_kernel_ptr_lie(int precision, int block, int blocks_per_sm);
+// The three-flavour exponential integrators' step kernels (kernels_3f_lie.cu).
+const void* step_kernel_ptr_3f_exp(int precision, int integrator);
 // The extended bulb model's step kernels (two flavours, up to 256 threads, one block per SM).
 const void* step_kernel_ptr_2e(int precision, int integrator, int block);
 }  // namespace xflat

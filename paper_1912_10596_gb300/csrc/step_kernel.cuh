@@ -370,6 +370,8 @@ struct Phys2 {
 #pragma unroll
     for (int i = 0; i < 3; ++i) y[i] *= inv;
   }
+  // the pure-state projection of the exponential steps: for a Bloch vector, its unit length
+  __device__ static inline void purify(Real (&y)[3]) { normalise(y); }
 };
 
 // Three flavours: the state is the full 3x3 Hermitian density matrix (9 reals: P00, P11, P22,
@@ -475,6 +477,51 @@ struct Phys3 {
     return m * sqrt(d + 2 * o);
   }
   __device__ static inline void normalise(Real (&)[9]) {}
+  // Mixed-precision exponential steps: restore the idempotency of the (pure) density matrix that
+  // the FP32 rounding of the propagators erodes step by step, P <- 3 P^2 - 2 P^3 (McWeeny
+  // purification: an eigenvalue 1 - e goes to 1 - 3 e^2 + 2 e^3, a small one d to 3 d^2 - 2 d^3),
+  // as the two-flavour path renormalises its Bloch vector.
+  __device__ static inline void purify(Real (&y)[9]) {
+    const Real pr[3][3] = {{y[0], y[3], y[5]}, {y[3], y[1], y[7]}, {y[5], y[7], y[2]}};
+    const Real pi[3][3] = {{0, y[4], y[6]}, {-y[4], 0, y[8]}, {-y[6], -y[8], 0}};
+    Real qr[3][3], qi[3][3];                          // P^2
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        Real sr = 0, si = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          sr += pr[a][c] * pr[c][b] - pi[a][c] * pi[c][b];
+          si += pr[a][c] * pi[c][b] + pi[a][c] * pr[c][b];
+        }
+        qr[a][b] = sr;
+        qi[a][b] = si;
+      }
+    Real outr[3][3], outi[3][3];                      // 3 P^2 - 2 P^3, upper triangle
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b) {
+        Real sr = 0, si = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          sr += qr[a][c] * pr[c][b] - qi[a][c] * pi[c][b];
+          si += qr[a][c] * pi[c][b] + qi[a][c] * pr[c][b];
+        }
+        outr[a][b] = Real(3) * qr[a][b] - Real(2) * sr;
+        outi[a][b] = Real(3) * qi[a][b] - Real(2) * si;
+      }
+    y[0] = outr[0][0];
+    y[1] = outr[1][1];
+    y[2] = outr[2][2];
+    y[3] = outr[0][1];
+    y[4] = outi[0][1];
+    y[5] = outr[0][2];
+    y[6] = outi[0][2];
+    y[7] = outr[1][2];
+    y[8] = outi[1][2];
+  }
   template <class Acc>
   __device__ static inline void accum_row(Acc& acc, Real w, const Real* row, const Real (&y)[NC]) {
     accum(acc, w, t1(row), y);
@@ -578,6 +625,7 @@ struct Phys2E {
   __device__ static inline Real tnorm2(const Real (&y)[3]) { return Phys2<Real>::tnorm2(y); }
   __device__ static inline Real enorm(const Real (&e)[3]) { return Phys2<Real>::enorm(e); }
   __device__ static inline void normalise(Real (&y)[3]) { Phys2<Real>::normalise(y); }
+  __device__ static inline void purify(Real (&y)[3]) { Phys2<Real>::normalise(y); }
 };
 
 
@@ -1051,6 +1099,184 @@ __device__ __forceinline__ void rotate(const Real (&Om)[3], Real (&y)[3]) {
   y[2] += a * c2 + b * d2;
 }
 
+// Three flavours: one cyclic-Jacobi rotation of the Hermitian matrix A (real and imaginary parts)
+// in the plane (p, q), accumulated into V: a phase makes A_pq real, then the real symmetric 2 x 2
+// Schur rotation (Golub and Van Loan, Matrix Computations, Sec. 8.5.2) zeroes it.
+template <typename Real>
+__device__ __forceinline__ void jacobi3_rotate(Real (&ar)[3][3], Real (&ai)[3][3], Real (&vr)[3][3],
+                                               Real (&vi)[3][3], int p, int q) {
+  const Real br = ar[p][q], bi = ai[p][q];
+  const Real mag = hypot(br, bi);                      // no underflow of the squares: |exp(i phi)| = 1
+  // an entry below the rounding of the diagonal is dropped (also keeps converged entries, which
+  // fall towards the underflow range sweep after sweep, from ever entering the phase)
+  const Real tiny = sizeof(Real) == 8 ? Real(8.673617379884035e-19) : Real(9.313225746154785e-10);   // 2^-60, 2^-30
+  if (!(mag > tiny * (fabs(ar[p][p]) + fabs(ar[q][q])))) {
+    ar[p][q] = ar[q][p] = ai[p][q] = ai[q][p] = Real(0);
+    return;
+  }
+  const Real er = br / mag, ei = bi / mag;             // exp(i phi) of A_pq
+  // A <- D^dagger A D, V <- V D with D = diag(1, exp(-i phi)) in the plane: A_pq becomes |A_pq|
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const Real xr = ar[k][q], xi = ai[k][q];
+    ar[k][q] = xr * er + xi * ei;
+    ai[k][q] = xi * er - xr * ei;
+    const Real wr = vr[k][q], wi = vi[k][q];
+    vr[k][q] = wr * er + wi * ei;
+    vi[k][q] = wi * er - wr * ei;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const Real xr = ar[q][k], xi = ai[q][k];
+    ar[q][k] = xr * er - xi * ei;
+    ai[q][k] = xi * er + xr * ei;
+  }
+  // real rotation J = [[c, s], [-s, c]] in the plane: A <- J^T A J, V <- V J
+  const Real tau = (ar[q][q] - ar[p][p]) / (Real(2) * mag);
+  const Real at = fabs(tau);
+  const Real big = sizeof(Real) == 8 ? Real(1e150) : Real(1e18);
+  const Real t = at > big ? Real(0.5) / tau : copysign(Real(1), tau) / (at + sqrt(Real(1) + tau * tau));
+  const Real c = Real(1) / sqrt(Real(1) + t * t), sn = t * c;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Real x = ar[k][p], y = ar[k][q];
+    ar[k][p] = c * x - sn * y;
+    ar[k][q] = sn * x + c * y;
+    x = ai[k][p];
+    y = ai[k][q];
+    ai[k][p] = c * x - sn * y;
+    ai[k][q] = sn * x + c * y;
+    x = vr[k][p];
+    y = vr[k][q];
+    vr[k][p] = c * x - sn * y;
+    vr[k][q] = sn * x + c * y;
+    x = vi[k][p];
+    y = vi[k][q];
+    vi[k][p] = c * x - sn * y;
+    vi[k][q] = sn * x + c * y;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Real x = ar[p][k], y = ar[q][k];
+    ar[p][k] = c * x - sn * y;
+    ar[q][k] = sn * x + c * y;
+    x = ai[p][k];
+    y = ai[q][k];
+    ai[p][k] = c * x - sn * y;
+    ai[q][k] = sn * x + c * y;
+  }
+  ar[p][q] = ar[q][p] = ai[p][q] = ai[q][p] = Real(0);
+}
+
+// Three flavours: y <- U y U^dagger with U = exp(-i Om) for Hermitian Om (9 reals: the diagonal,
+// then real and imaginary parts of the 01, 02 and 12 entries), the propagator of Eq. U for a
+// 3 x 3 generator.  Om = V diag(l) V^dagger by cyclic Jacobi sweeps (a 3 x 3 Hermitian matrix
+// converges quadratically: to the working precision in four sweeps, five in FP64); in the
+// eigenbasis the entry (a, b) of V^dagger y V turns by exp(-i (l_a - l_b)), so U is never formed.
+template <typename Real>
+__device__ __noinline__ void propagate3(const Real (&Om)[9], Real (&y)[9]) {
+  constexpr int kSweeps = sizeof(Real) == 8 ? 5 : 4;
+  Real ar[3][3] = {{Om[0], Om[3], Om[5]}, {Om[3], Om[1], Om[7]}, {Om[5], Om[7], Om[2]}};
+  Real ai[3][3] = {{0, Om[4], Om[6]}, {-Om[4], 0, Om[8]}, {-Om[6], -Om[8], 0}};
+  Real vr[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  Real vi[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll 1
+  for (int sw = 0; sw < kSweeps; ++sw) {
+    jacobi3_rotate(ar, ai, vr, vi, 0, 1);
+    jacobi3_rotate(ar, ai, vr, vi, 0, 2);
+    jacobi3_rotate(ar, ai, vr, vi, 1, 2);
+  }
+  const Real yr[3][3] = {{y[0], y[3], y[5]}, {y[3], y[1], y[7]}, {y[5], y[7], y[2]}};
+  const Real yi[3][3] = {{0, y[4], y[6]}, {-y[4], 0, y[8]}, {-y[6], -y[8], 0}};
+  // T = Y V, W = V^dagger T
+  Real tr[3][3], ti[3][3], wr[3][3], wi[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      Real sr = 0, si = 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sr += yr[a][c] * vr[c][b] - yi[a][c] * vi[c][b];
+        si += yr[a][c] * vi[c][b] + yi[a][c] * vr[c][b];
+      }
+      tr[a][b] = sr;
+      ti[a][b] = si;
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      Real sr = 0, si = 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sr += vr[c][a] * tr[c][b] + vi[c][a] * ti[c][b];
+        si += vr[c][a] * ti[c][b] - vi[c][a] * tr[c][b];
+      }
+      wr[a][b] = sr;
+      wi[a][b] = si;
+    }
+  // the phases of the off-diagonal entries in the eigenbasis (W stays Hermitian)
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a + 1; b < 3; ++b) {
+      Real sd, cd;
+      if (sizeof(Real) == 4) sincosf((float)(ar[a][a] - ar[b][b]), (float*)&sd, (float*)&cd);
+      else sincos((double)(ar[a][a] - ar[b][b]), (double*)&sd, (double*)&cd);
+      const Real xr = wr[a][b], xi = wi[a][b];
+      wr[a][b] = xr * cd + xi * sd;
+      wi[a][b] = xi * cd - xr * sd;
+      wr[b][a] = wr[a][b];
+      wi[b][a] = -wi[a][b];
+    }
+  // T = V W, Y = T V^dagger (upper triangle)
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      Real sr = 0, si = 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sr += vr[a][c] * wr[c][b] - vi[a][c] * wi[c][b];
+        si += vr[a][c] * wi[c][b] + vi[a][c] * wr[c][b];
+      }
+      tr[a][b] = sr;
+      ti[a][b] = si;
+    }
+  Real outr[3][3], outi[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b) {
+      Real sr = 0, si = 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sr += tr[a][c] * vr[b][c] + ti[a][c] * vi[b][c];
+        si += ti[a][c] * vr[b][c] - tr[a][c] * vi[b][c];
+      }
+      outr[a][b] = sr;
+      outi[a][b] = si;
+    }
+  y[0] = outr[0][0];
+  y[1] = outr[1][1];
+  y[2] = outr[2][2];
+  y[3] = outr[0][1];
+  y[4] = outi[0][1];
+  y[5] = outr[0][2];
+  y[6] = outi[0][2];
+  y[7] = outr[1][2];
+  y[8] = outi[1][2];
+}
+
+// The propagator of Eq. U over one step for the generator Om (step length and coefficients folded
+// in): y <- exp(-i Om) y exp(i Om).  Two flavours: the rotation of the Bloch vector; three
+// flavours: by the eigen-decomposition of Om.
+template <typename Real>
+__device__ __forceinline__ void propagate(const Real (&Om)[3], Real (&y)[3]) { rotate(Om, y); }
+template <typename Real>
+__device__ __forceinline__ void propagate(const Real (&Om)[9], Real (&y)[9]) { propagate3(Om, y); }
+
 // Per-block shared state of the piece being processed.
 template <typename Real, class Phys>
 struct BlockShared {
@@ -1296,58 +1522,62 @@ struct PassBody<Phys, Tab, Real, false, kPass, kKind> {
 // Commutator-free Lie RK4 on Bloch vectors (two flavours) ---------------------------------------
 template <class Phys, class Tab, typename Real, int kPass, int kKind>
 struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
-  static constexpr int NC = 3;
+  static constexpr int NC = Phys::NC;          // 3: Bloch vectors; 9: Hermitian 3 x 3 matrices
   static constexpr bool kStore = false;
   // rotation of y by d K (the propagator of Eq. U over the path length d for generator K)
-  __device__ static inline void rot(Real (&y)[3], const Real (&K)[3], Real d) {
-    Real Om[3] = {d * K[0], d * K[1], d * K[2]};
-    rotate(Om, y);
+  __device__ static inline void rot(Real (&y)[NC], const Real (&K)[NC], Real d) {
+    Real Om[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) Om[i] = d * K[i];
+    propagate(Om, y);
   }
   // the fourth stage state of a CF4 step of size hh from y with generators Ka (its first stage)
   // and Kc (its third): exp(hh (Kc - Ka/2)) exp(hh/2 Ka) y
-  __device__ static inline void cf4_stage4(Real (&y)[3], const Real (&Ka)[3], const Real (&Kc)[3], Real hh) {
+  __device__ static inline void cf4_stage4(Real (&y)[NC], const Real (&Ka)[NC], const Real (&Kc)[NC], Real hh) {
     rot(y, Ka, Real(0.5) * hh);
-    const Real D[3] = {Kc[0] - Real(0.5) * Ka[0], Kc[1] - Real(0.5) * Ka[1], Kc[2] - Real(0.5) * Ka[2]};
+    Real D[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) D[i] = Kc[i] - Real(0.5) * Ka[i];
     rot(y, D, hh);
   }
   // the CF4 update of size hh from y with the step's four generators
-  __device__ static inline void cf4_final(Real (&y)[3], const Real (&K1)[3], const Real (&K2)[3],
-                                          const Real (&K3)[3], const Real (&K4)[3], Real hh) {
-    Real Om[3];
+  __device__ static inline void cf4_final(Real (&y)[NC], const Real (&K1)[NC], const Real (&K2)[NC],
+                                          const Real (&K3)[NC], const Real (&K4)[NC], Real hh) {
+    Real Om[NC];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < NC; ++i)
       Om[i] = hh * (Real(0.25) * K1[i] + Real(1.0 / 6.0) * (K2[i] + K3[i]) - Real(1.0 / 12.0) * K4[i]);
-    rotate(Om, y);
+    propagate(Om, y);
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < NC; ++i)
       Om[i] = hh * (Real(-1.0 / 12.0) * K1[i] + Real(1.0 / 6.0) * (K2[i] + K3[i]) + Real(0.25) * K4[i]);
-    rotate(Om, y);
+    propagate(Om, y);
   }
   template <class BS>
   __device__ static inline void gen(const BS& bs, const typename Phys::Beam& bm, const TabView<Real, Phys>& tv,
-                                    int tj, int s, Real (&K)[3]) {
+                                    int tj, int s, Real (&K)[NC]) {
     Phys::K(tv.row(s, tj), bm, bs.vac, bs.scr[s], K);
   }
   // Richardson-controlled CF4 (TabCFR): pass p forms the stage state of slot p + 2 from y; the
   // final pass forms both results, the error ratio and the moments of the kept result.
   template <class BS, class Acc>
   __device__ static inline void richardson(const BS& bs, const typename Phys::Beam& bm,
-                                           const TabView<Real, Phys>& tv, int tj, Real (&y)[3], Acc& acc,
+                                           const TabView<Real, Phys>& tv, int tj, Real (&y)[NC], Acc& acc,
                                            Real& emax, int& bad, bool mixed) {
     const Real h = bs.hB[0], hh = Real(0.5) * h;
     constexpr int I = kKind == kFinalPass ? 0 : kPass + 2;   // slot formed by this pass
-    Real K1[3];
+    Real K1[NC];
     gen(bs, bm, tv, tj, 1, K1);
     if constexpr (I >= 2 && I <= 4) {
       // full step: Y2 = exp(h/2 K1) y, Y3 = exp(h/2 K2) y, Y4 = exp(h (K3 - K1/2)) exp(h/2 K1) y
       if constexpr (I == 2) {
         rot(y, K1, hh);
       } else if constexpr (I == 3) {
-        Real K2[3];
+        Real K2[NC];
         gen(bs, bm, tv, tj, 2, K2);
         rot(y, K2, hh);
       } else {
-        Real K3[3];
+        Real K3[NC];
         gen(bs, bm, tv, tj, 3, K3);
         cf4_stage4(y, K1, K3, h);
       }
@@ -1359,11 +1589,11 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
       if constexpr (I == 5) {
         rot(y, K1, Real(0.5) * hh);
       } else if constexpr (I == 6) {
-        Real K5[3];
+        Real K5[NC];
         gen(bs, bm, tv, tj, 5, K5);
         rot(y, K5, Real(0.5) * hh);
       } else {
-        Real K6[3];
+        Real K6[NC];
         gen(bs, bm, tv, tj, 6, K6);
         cf4_stage4(y, K1, K6, hh);
       }
@@ -1371,9 +1601,11 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
       return;
     }
     // everything later starts from the first half step's result y_a (slot 8)
-    Real y0[3] = {y[0], y[1], y[2]};
+    Real y0[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) y0[i] = y[i];
     {
-      Real K5[3], K6[3], K7[3];
+      Real K5[NC], K6[NC], K7[NC];
       gen(bs, bm, tv, tj, 5, K5);
       gen(bs, bm, tv, tj, 6, K6);
       gen(bs, bm, tv, tj, 7, K7);
@@ -1383,17 +1615,17 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
       Phys::accum_row(acc, bm.w, tv.row(8, tj), y);
       return;
     }
-    Real K8[3];
+    Real K8[NC];
     gen(bs, bm, tv, tj, 8, K8);
     if constexpr (I >= 9 && I <= 11) {
       if constexpr (I == 9) {
         rot(y, K8, Real(0.5) * hh);
       } else if constexpr (I == 10) {
-        Real K9[3];
+        Real K9[NC];
         gen(bs, bm, tv, tj, 9, K9);
         rot(y, K9, Real(0.5) * hh);
       } else {
-        Real K10[3];
+        Real K10[NC];
         gen(bs, bm, tv, tj, 10, K10);
         cf4_stage4(y, K8, K10, hh);
       }
@@ -1402,30 +1634,32 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
     } else {
       // final pass: y_b = the second half step from y_a, y_full = the full step from y0
       {
-        Real K9[3], K10[3], K11[3];
+        Real K9[NC], K10[NC], K11[NC];
         gen(bs, bm, tv, tj, 9, K9);
         gen(bs, bm, tv, tj, 10, K10);
         gen(bs, bm, tv, tj, 11, K11);
         cf4_final(y, K8, K9, K10, K11, hh);
       }
-      Real yf[3] = {y0[0], y0[1], y0[2]};
+      Real yf[NC];
+#pragma unroll
+      for (int i = 0; i < NC; ++i) yf[i] = y0[i];
       {
-        Real K2[3], K3[3], K4[3];
+        Real K2[NC], K3[NC], K4[NC];
         gen(bs, bm, tv, tj, 2, K2);
         gen(bs, bm, tv, tj, 3, K3);
         gen(bs, bm, tv, tj, 4, K4);
         cf4_final(yf, K1, K2, K3, K4, h);
       }
-      Real e[3];
+      Real e[NC];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) e[i] = (y[i] - yf[i]) * Real(1.0 / 15.0);
+      for (int i = 0; i < NC; ++i) e[i] = (y[i] - yf[i]) * Real(1.0 / 15.0);
       if (!(Phys::tnorm2(y0) <= rbig<Real>())) bad = 1;       // non-finite input state: fatal
       const bool ynok = Phys::tnorm2(y) <= rbig<Real>();
       const Real den = bs.atol + bs.rtol * sqrt(fmax(Phys::tnorm2(y0), Phys::tnorm2(y)));
       Real r2 = Phys::tnorm2(e) / (den * den);
       if (!(r2 <= rbig<Real>()) || !ynok) r2 = Real(INFINITY);
       emax = fmax(emax, r2);
-      if (mixed && ynok) Phys::normalise(y);
+      if (mixed && ynok) Phys::purify(y);
       Phys::accum_row(acc, bm.w, tv.row(11, tj), y);
     }
   }
@@ -1447,75 +1681,75 @@ struct PassBody<Phys, Tab, Real, true, kPass, kKind> {
     if constexpr (Tab::kEM2) {
       // exponential midpoint rule: half step with K1 -> Y_half (moments at r + h/2); final pass:
       // y' = exp(h K2) y, the estimate exp(h K1) y, the error ratio, moments of y' at r + h
-      Real K1[3], Om[3];
+      Real K1[NC], Om[NC];
       Phys::K(tv.row(1, tj), bm, bs.vac, bs.scr[1], K1);
       if (kKind == kStagePass) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) Om[i] = Real(0.5) * h * K1[i];
-        rotate(Om, y);
+        for (int i = 0; i < NC; ++i) Om[i] = Real(0.5) * h * K1[i];
+        propagate(Om, y);
         Phys::accum_row(acc, bm.w, tv.row(2, tj), y);
         return;
       }
-      Real K2[3], yn[3], ye[3], e[3];
+      Real K2[NC], yn[NC], ye[NC], e[NC];
       Phys::K(tv.row(2, tj), bm, bs.vac, bs.scr[2], K2);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) { yn[i] = y[i]; ye[i] = y[i]; Om[i] = h * K2[i]; }
-      rotate(Om, yn);
+      for (int i = 0; i < NC; ++i) { yn[i] = y[i]; ye[i] = y[i]; Om[i] = h * K2[i]; }
+      propagate(Om, yn);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) Om[i] = h * K1[i];
-      rotate(Om, ye);
+      for (int i = 0; i < NC; ++i) Om[i] = h * K1[i];
+      propagate(Om, ye);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) e[i] = yn[i] - ye[i];
+      for (int i = 0; i < NC; ++i) e[i] = yn[i] - ye[i];
       if (!(Phys::tnorm2(y) <= rbig<Real>())) bad = 1;       // non-finite input state: fatal
       const bool ynok = Phys::tnorm2(yn) <= rbig<Real>();
       const Real den = bs.atol + bs.rtol * sqrt(fmax(Phys::tnorm2(y), Phys::tnorm2(yn)));
       Real r2 = Phys::tnorm2(e) / (den * den);
       if (!(r2 <= rbig<Real>()) || !ynok) r2 = Real(INFINITY);
       emax = fmax(emax, r2);
-      if (mixed && ynok) Phys::normalise(yn);
+      if (mixed && ynok) Phys::purify(yn);
       Phys::accum_row(acc, bm.w, tv.row(3, tj), yn);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) y[i] = yn[i];
+      for (int i = 0; i < NC; ++i) y[i] = yn[i];
       return;
     }
-    Real K1[3], K2[3], K3[3], K4[3], Om[3];
+    Real K1[NC], K2[NC], K3[NC], K4[NC], Om[NC];
     Phys::K(tv.row(1, tj), bm, bs.vac, bs.scr[1], K1);
     if (kKind == kStagePass && kPass == 0) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) Om[i] = Real(0.5) * h * K1[i];
-      rotate(Om, y);
+      for (int i = 0; i < NC; ++i) Om[i] = Real(0.5) * h * K1[i];
+      propagate(Om, y);
       Phys::accum_row(acc, bm.w, tv.row(2, tj), y);
       return;
     }
     Phys::K(tv.row(2, tj), bm, bs.vac, bs.scr[2], K2);
     if (kKind == kStagePass && kPass == 1) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) Om[i] = Real(0.5) * h * K2[i];
-      rotate(Om, y);
+      for (int i = 0; i < NC; ++i) Om[i] = Real(0.5) * h * K2[i];
+      propagate(Om, y);
       Phys::accum_row(acc, bm.w, tv.row(3, tj), y);
       return;
     }
     Phys::K(tv.row(3, tj), bm, bs.vac, bs.scr[3], K3);
     if (kKind == kStagePass && kPass == 2) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) Om[i] = Real(0.5) * h * K1[i];
-      rotate(Om, y);
+      for (int i = 0; i < NC; ++i) Om[i] = Real(0.5) * h * K1[i];
+      propagate(Om, y);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) Om[i] = h * K3[i] - Real(0.5) * h * K1[i];
-      rotate(Om, y);
+      for (int i = 0; i < NC; ++i) Om[i] = h * K3[i] - Real(0.5) * h * K1[i];
+      propagate(Om, y);
       Phys::accum_row(acc, bm.w, tv.row(4, tj), y);
       return;
     }
     Phys::K(tv.row(4, tj), bm, bs.vac, bs.scr[4], K4);
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < NC; ++i)
       Om[i] = h * (Real(0.25) * K1[i] + Real(1.0 / 6.0) * (K2[i] + K3[i]) - Real(1.0 / 12.0) * K4[i]);
-    rotate(Om, y);
+    propagate(Om, y);
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < NC; ++i)
       Om[i] = h * (Real(-1.0 / 12.0) * K1[i] + Real(1.0 / 6.0) * (K2[i] + K3[i]) + Real(0.25) * K4[i]);
-    rotate(Om, y);
-    if (mixed) Phys::normalise(y);
+    propagate(Om, y);
+    if (mixed) Phys::purify(y);
     Phys::accum_row(acc, bm.w, tv.row(4, tj), y);
   }
 };

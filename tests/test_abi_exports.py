@@ -57,12 +57,9 @@ def test_create_rejects_bad_config_before_touching_the_gpu(lib_path):
     c.abi_version = 99
     assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_INVAL
     c = xflat.default_config()
-    c.integrator = xflat.LIE_RK4
-    c.n_flavor = 3
-    assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_UNSUPPORTED
-    c.integrator = xflat.EXP_MIDPOINT
-    assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_UNSUPPORTED
     c.integrator = xflat.LIE_ADAPTIVE
+    c.n_flavor = 3
+    c.n_phi = 4                                     # the extended model is two-flavour only
     assert xflat.xflat_create(ctypes.byref(c), ctypes.byref(h)) == xflat.ERR_UNSUPPORTED
     c = xflat.default_config()
     c.integrator = xflat.LIE_ADAPTIVE

@@ -655,3 +655,37 @@ def test_matter_table_reproduces_a_power_law():
     Ya, _ = evolve_fixed(Bulb(pl), Bulb(pl).initial_state(), 300.0, 301.0, 50, "lie_rk4")
     Yb, _ = evolve_fixed(Bulb(tab), Bulb(tab).initial_state(), 300.0, 301.0, 50, "lie_rk4")
     assert np.abs(Ya - Yb).max() < 1e-12
+
+
+def test_lie_adaptive_three_flavours_meets_the_vacuum_closed_form():
+    """The adaptive commutator-free Lie RK4 on three flavours (eigendecomposition propagators):
+    mu = lambda = 0 with every mixing angle and both splittings non-zero, 11 -> 211 km with a
+    tolerance of 1e-10, reproduces the textbook three-flavour vacuum P_ee and P_emu (as in
+    test_three_flavour_vacuum_closed_form) in a few hundred steps, and its steps grow far beyond the
+    first one."""
+    from oracle.integrate import evolve_lie_adaptive
+    th, dm = (0.59, 0.15, 0.785), (7.5e-5, 2.4e-3)
+    wl = Workload(name="vac3a", n_flavor=3, n_energy=6, n_angle=4, E_min=2.0, E_max=20.0, L=NO_L,
+                  dm2=dm, theta=th)
+    b = Bulb(wl)
+    Y, r, st = evolve_lie_adaptive(b, b.initial_state(), 11.0, 211.0, 1e-10, 1e-10, 0.01, max_attempts=5000)
+    assert r == 211.0 and st.accepted < 2000
+    assert max(h for _, h, ok in st.steps if ok) > 50 * st.steps[0][1]
+    c12, s12 = math.cos(th[0]), math.sin(th[0])
+    c13, s13 = math.cos(th[1]), math.sin(th[1])
+    c23, s23 = math.cos(th[2]), math.sin(th[2])
+    Ue = [c12 * c13, s12 * c13, s13]
+    Um = [-s12 * c23 - c12 * s23 * s13, c12 * c23 - s12 * s23 * s13, s23 * c13]
+    m2 = [0.0, dm[0], dm[1]]
+    g = b.grid
+    L = 211.0 * cos_theta(g.u, 11.0, 211.0) - 11.0 * np.sqrt(1.0 - g.u)
+    k = 1.0 / (4 * ph.HBARC_EV_KM * 1e6)
+    Pee, Pem = np.ones((4, 6)), np.zeros((4, 6))
+    for i in range(3):
+        for j in range(i + 1, 3):
+            s2 = np.sin(k * (m2[j] - m2[i]) * L[:, None] / g.E[None, :]) ** 2
+            Pee -= 4 * Ue[i] ** 2 * Ue[j] ** 2 * s2
+            Pem -= 4 * Ue[i] * Um[i] * Ue[j] * Um[j] * s2
+    for s in range(2):
+        assert np.abs(Y[s, ..., 0, 0].real - Pee).max() < 1e-7
+        assert np.abs(Y[s, ..., 1, 1].real - Pem).max() < 1e-7
