@@ -566,6 +566,12 @@ def measure_configs(only=None):
         range_run(big, "fp64", "lie_adaptive", 1e-6, big.r1)
         range_run(big, "fp64", "lie_adaptive", 1e-9, big.r1)
         range_run(big, "mixed", "dp45", 1e-6, big.r1, n_per_launch=256)
+        # three flavours, both hierarchies: the adaptive exact propagators (3 x 3 Eq. U by
+        # eigen-decomposition) over the whole 11 -> 1000 km, and explicit DP45 from R for comparison
+        for dm31 in (2.4e-3, -2.4e-3):
+            wl3 = workload_3f_fp64(dm31)
+            range_run(wl3, "mixed", "lie_adaptive", 1e-6, wl3.r1)
+            range_run(wl3, "fp64", "lie_adaptive", 1e-6, wl3.r1)
         wl3 = workload_3f_fp64()
         range_run(wl3, "fp64", "dp45", 1e-9, wl3.r1, n_per_launch=256)
     if not want("adjoint"):
