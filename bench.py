@@ -34,14 +34,14 @@ L2_BYTES = 129 * 1024 * 1024
 # DRAM traffic of one timed launch of the step kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of an 8-step launch after the L2 flush).  It holds only for that launch size and for the kernel
 # code it was taken on, identified by kernel_code_hash(); otherwise the benchmark reports null.
-STEP_TRAFFIC = {"bytes_per_launch": 54799104 + 178418176, "steps_per_launch": 8,
-                "code_sha256": "85bf3e2f915848f738f63cb341223ed7621d79945e0aa0656c60c80a3cafa363"}
+STEP_TRAFFIC = {"bytes_per_launch": 51212800 + 173520640, "steps_per_launch": 8,
+                "code_sha256": "384a7fc295b4893c6b375e919685cf6890297471778ed692739cffb47e9a3cb5"}
 KERNEL_SOURCES = ["step_kernel.cuh", "xflat_internal.cuh", "kernels_2f.cu"]
 # Warp instructions of one radial step of the same kernel code (smsp__inst_executed.sum of one ncu
 # capture of a one-step launch, which also carries the launch's first set-up, so a step inside a
 # longer launch issues a little less): with the step time and the sampled SM clock it gives the
 # kernel's place under its instruction-issue ceiling (4 warp instructions per clock per SM).
-STEP_INSTRUCTIONS = {"warp_inst_per_step": 132210830, "code_sha256": STEP_TRAFFIC["code_sha256"]}
+STEP_INSTRUCTIONS = {"warp_inst_per_step": 132219345, "code_sha256": STEP_TRAFFIC["code_sha256"]}
 
 
 def issue_roofline(ms_per_step, sm_mhz, n_sm):
