@@ -1,5 +1,6 @@
 """Small runs of every step-kernel family through the library the binding loads (XFLAT_VARIANT
-selects a checking build): two and three flavours, FP64 and mixed precision, each integrator, the
+selects a checking build): two and three flavours (three also with the adaptive exponential
+integrator), FP64 and mixed precision, each integrator, the
 extended bulb model, the single-angle geometry with a matter table, a batch of uneven instances
 (dynamic piece scheduling) and two beam shards, each over a ragged beam count.  `run_cases()`
 returns the final states and moments by case name; as a script it writes them to an .npz file, so
@@ -53,6 +54,12 @@ def run_cases(xf):
                                          integrator="dp45", h0=0.05, n_energy=13, n_angle=11), 100.0, 100.5)
     _single(xf, out, "mixed_ext", Workload(name="c8", integrator="dp45", precision="mixed", rtol=1e-6, atol=1e-6,
                                            h0=0.05, n_energy=13, n_angle=11), 100.0, 100.5, n_phi=4)
+    _single(xf, out, "fp64_3f_lie", Workload(name="c10", n_flavor=3, dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.78),
+                                             integrator="lie_adaptive", h0=0.05, n_energy=13, n_angle=11),
+            100.0, 100.5)
+    _single(xf, out, "mixed_3f_lie", Workload(name="c11", n_flavor=3, dm2=(7.5e-5, 2.4e-3), theta=(0.59, 0.15, 0.78),
+                                              integrator="lie_adaptive", precision="mixed", rtol=1e-6, atol=1e-6,
+                                              h0=0.05, n_energy=13, n_angle=11), 100.0, 100.5)
     rt = [11.0, 50.0, 200.0, 1000.0]
     _single(xf, out, "fp64_single_table",
             Workload(name="c9", integrator="dp45", h0=0.05, matter="table", matter_table_r=rt,
