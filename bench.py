@@ -522,10 +522,10 @@ def measure_configs(only=None):
         line(wl.name, nb, bsu, ms, 16, 14.0, window="16 DP45 steps from 11 km",
              block_size=sv.stats().block_size, blocks=sv.stats().grid_blocks)
         sv.close()
-    # the configured radial ranges from r = R: the 4M-beam case with the adaptive exact propagators
-    # (mixed at rtol 1e-6 over all of 11 -> 500 km; FP64 at 1e-6 and 1e-9 for a bounded wall time),
-    # and the explicit DP45 step near R for comparison (mixed 4M beams; FP64 three flavours, the
-    # exponential schemes being two-flavour only)
+    # the configured radial ranges from r = R with the adaptive exact propagators: the 4M-beam case
+    # (mixed at rtol 1e-6 over all of 11 -> 500 km; FP64 at 1e-6 and 1e-9 for a bounded wall time)
+    # and the three-flavour case over 11 -> 1000 km (mixed; FP64 for a bounded wall time), and the
+    # explicit DP45 step near R for comparison (mixed 4M beams; FP64 three flavours)
     if want("range"):
         from bulb_inputs import workload_2f_large
         budget = 30.0
