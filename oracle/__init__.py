@@ -17,4 +17,15 @@ expm       Eq. U (2x2 closed form) and a Hermitian 3x3 exponential by eigendecom
 integrate  fixed-step RK4, adaptive Dormand-Prince 5(4), commutator-free Lie RK4 (CF4)
 four_psi   the paper-literal four-wavefunction state (nu_e, nu_x, nubar_e, nubar_x per beam)
 adjoint    discrete adjoint of fixed-step RK4 for the survival-probability objective
+extended   the extended bulb model (azimuthal bins, four moments)
+
+Pins (tests/test_oracle_pins.py, test_oracle_adjoint.py, test_oracle_extended.py, each mistake of
+tests/test_oracle_mutations.py failing at least one): every function above is held by closed
+forms (vacuum and constant-density oscillations in two and three flavours, the synchronised
+collective precession), invariants (unit Bloch vectors, lepton number, trace and purity),
+reductions (three flavours to two, single angle to the radial beam, extended to bulb, the four
+wavefunctions to two states), hand-computed moments and textbook matter strengths, integrator
+orders and exactness for constant generators, and finite differences for the adjoint.  The full
+multi-angle nonlinear result of a bulb run is pinned only through those parts: the paper prints no
+number for it, so beyond them its parity is unpinned.
 """
