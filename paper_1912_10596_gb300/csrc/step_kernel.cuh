@@ -13,8 +13,12 @@
 //       state buffer and reduce either the moments of the new state (fixed step) or the error norm
 //       (DP45).
 //
-// So every pass reads each beam's state once (vector loads of the SoA planes) and a step writes it
-// once; the FP64 kernels also move their stage planes.
+// So every pass reads each beam's state once (vector loads of the SoA planes, or the per-thread
+// cp.async ring of the FP32 two-flavour bulb kernels) and a step writes it once; the FP64 kernels
+// also move their stage planes.  The exponential integrators (commutator-free Lie RK4, the
+// exponential midpoint rule, the adaptive Lie RK4 with Richardson control) build every stage state
+// from y by exact propagators exp(-i Om) y exp(i Om) of Eq. U instead: a rotation of the Bloch
+// vector for two flavours, an eigen-decomposition of the 3 x 3 generator for three (propagate3).
 //
 // Moments without cancellation.  With the measure of Eq. Hnu in u-bins, the nu-nu term of beam b is
 // mu(r) (J0 - cos(th_b) J1), J0 = sum w s / cos(th), J1 = sum w s.  Far from the neutrino sphere
