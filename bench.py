@@ -295,8 +295,9 @@ def matched_error(xf, torch, log=None):
     Windows (no matter, so that the collective flavour evolution of the small case's physics
     happens inside them): the 4M-beam grid over 100 -> 110 km; the 64 batched instances over
     100 -> 101 km, the mixed form all instances in one persistent launch per chunk of steps, the
-    FP64 path one instance after another."""
-    from bulb_inputs import Workload, batched_workloads
+    FP64 path one instance after another; the three-flavour grid (256 E x 512 u) over
+    100 -> 102 km."""
+    from bulb_inputs import Workload, batched_workloads, workload_3f_fp64
     stream = torch.cuda.current_stream()
 
     def run(wls, precision, integrator, tol, r0, r1, per_instance):
@@ -354,7 +355,10 @@ def matched_error(xf, torch, log=None):
     for w in batch:
         w.matter = "none"
     batched = compare("batched", batch, 100.0, 101.0, True)
-    return single, batched
+    wl3 = workload_3f_fp64()
+    wl3.matter = "none"
+    three = compare("3f", [wl3], 100.0, 102.0, False)
+    return single, batched, three
 
 
 def compare_integrators():
@@ -710,10 +714,11 @@ def main():
                "median_of_repeats": True}
     matched = None
     if rank == 0 and not args.no_matched:
-        single, batched = matched_error(xf, torch, log=lambda m: print(m, file=sys.stderr))
+        single, batched, three = matched_error(xf, torch, log=lambda m: print(m, file=sys.stderr))
         matched = {"speedup_mixed_vs_fp64_at_1e-4": single["speedup_at_1e-4"],
                    "speedup_batched_vs_fp64_at_1e-4": batched["speedup_at_1e-4"],
-                   "single": single, "batched": batched}
+                   "speedup_mixed_vs_fp64_at_1e-4_three_flavours": three["speedup_at_1e-4"],
+                   "single": single, "batched": batched, "three_flavours": three}
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, n, dt, beams = cpu_baseline()
