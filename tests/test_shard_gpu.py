@@ -104,3 +104,31 @@ def test_shard_handle_rejects_the_plain_calls(xf):
     assert e.value.code == xf.ERR_STATE
     with pytest.raises(xf.XflatError):
         xf.Solver(xf.config_from_workload(wl), shard=(3, 64))      # lower bound not a multiple of 4
+
+
+@pytest.mark.parametrize("integrator,tol", [("dp45", 1e-9), ("lie_adaptive", 1e-9)])
+def test_three_flavour_shards(xf, integrator, tol):
+    """Three flavours (18 moment words per partial): two shard handles on the block boundaries take
+    the unsharded run's steps and reproduce its states (DP45 bit for bit; the adaptive exponential
+    integrator to 1e-12, as for two flavours)."""
+    wl = Workload(name="sh3f", n_flavor=3, n_energy=64, n_angle=160, dm2=(7.5e-5, 2.4e-3),
+                  theta=(0.59, 0.15, 0.785), integrator=integrator, rtol=tol, atol=tol, h0=0.5)
+    full = make_solver(xf, wl)
+    full.reset(100.0)
+    full.evolve(100.0, 101.0)
+    n = wl.n_beams
+    parts = shards_of(xf, wl, [(0, n // 2), (n // 2, n)])
+    for s in parts:
+        s.reset(100.0)
+    steps = shard.evolve_sharded(parts, 101.0)
+    st = full.stats()
+    assert steps == st.accepted + st.rejected
+    for s in parts:
+        assert (s.stats().accepted, s.stats().rejected) == (st.accepted, st.rejected)
+    ref = full.get_rho(xf.LAYOUT_NATIVE)
+    got = np.concatenate([parts[0].get_rho(xf.LAYOUT_NATIVE)[:, : n // 2],
+                          parts[1].get_rho(xf.LAYOUT_NATIVE)[:, n // 2:]], axis=1)
+    if integrator == "dp45":
+        assert np.array_equal(got, ref)
+    else:
+        assert np.abs(got - ref).max() < 1e-12
