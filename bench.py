@@ -565,6 +565,36 @@ def measure_configs(only=None):
             print(json.dumps(out), flush=True)
             sv.close()
 
+        def range_run_batch(wls, precision, integrator, tol, n_per_launch=64):
+            """All instances of a batch in one handle, each to its own configured end radius."""
+            cfgs = [xf.config_from_workload(w, precision=precision, integrator=integrator, rtol=tol, atol=tol,
+                                            h0_km=1e-9, steps_per_launch=n_per_launch) for w in wls]
+            sv = solver(cfgs, [w.spectra() for w in wls])
+            sv.reset(wls[0].r0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            sv.advance([w.r1 for w in wls], max_steps=n_per_launch)
+            while True:
+                done = sv.advance(None, max_steps=n_per_launch)
+                sts = [sv.stats(i) for i in range(len(wls))]
+                if done or any(x.status for x in sts) or time.perf_counter() - t0 > budget:
+                    break
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sts = [sv.stats(i) for i in range(len(wls))]
+            pmin = min(float(sv.pee(inst=i)[0].min()) for i in range(len(wls)))
+            out = {"workload": f"batched {len(wls)} instances (seed 0x5EED0003)", "integrator": integrator,
+                   "precision": precision, "rtol": tol, "beams": int(sum(w.n_beams for w in wls)),
+                   "r_start_km": wls[0].r0, "r_reached_km_min": min(x.r_km for x in sts),
+                   "r_target_km": wls[0].r1, "instances_done": sum(1 for x, w in zip(sts, wls) if x.r_km >= w.r1),
+                   "accepted_sum": int(sum(x.accepted for x in sts)), "rejected_sum": int(sum(x.rejected for x in sts)),
+                   "accepted_max": int(max(x.accepted for x in sts)), "status": [int(x.status) for x in sts if x.status],
+                   "device_ms": e0.elapsed_time(e1), "wall_s": time.perf_counter() - t0, "pee_min": pmin}
+            print(json.dumps(out), flush=True)
+            sv.close()
+
         big = workload_2f_large("mixed")
         range_run(big, "mixed", "lie_adaptive", 1e-6, big.r1)
         range_run(big, "fp64", "lie_adaptive", 1e-6, big.r1)
@@ -578,6 +608,8 @@ def measure_configs(only=None):
             range_run(wl3, "fp64", "lie_adaptive", 1e-6, wl3.r1)
         wl3 = workload_3f_fp64()
         range_run(wl3, "fp64", "dp45", 1e-9, wl3.r1, n_per_launch=256)
+        # the 64 batched instances over their configured 11 -> 300 km in one handle
+        range_run_batch(batched_workloads(), "mixed", "lie_adaptive", 1e-6)
     if not want("adjoint"):
         return
 
