@@ -530,7 +530,7 @@ def measure_configs(only=None):
     # (mixed at rtol 1e-6 over all of 11 -> 500 km; FP64 at 1e-6 and 1e-9 for a bounded wall time)
     # and the three-flavour case over 11 -> 1000 km (mixed; FP64 for a bounded wall time), and the
     # explicit DP45 step near R for comparison (mixed 4M beams; FP64 three flavours)
-    if want("range"):
+    if want("range") or only == "range3f":
         from bulb_inputs import workload_2f_large
         budget = 30.0
 
@@ -595,6 +595,12 @@ def measure_configs(only=None):
             print(json.dumps(out), flush=True)
             sv.close()
 
+        if only == "range3f":
+            # the three-flavour configured range alone (normal hierarchy, mixed): a short command
+            # for profiling the three-flavour exponential kernel
+            wl3 = workload_3f_fp64()
+            range_run(wl3, "mixed", "lie_adaptive", 1e-6, wl3.r1)
+            return
         big = workload_2f_large("mixed")
         range_run(big, "mixed", "lie_adaptive", 1e-6, big.r1)
         range_run(big, "fp64", "lie_adaptive", 1e-6, big.r1)
@@ -649,7 +655,7 @@ def main():
                     help="accuracy against cost of the integrators on the 4096-beam case instead of the benchmark")
     ap.add_argument("--configs", action="store_true",
                     help="device rates of the other workloads (small, three-flavour, batched, adjoint) instead of the benchmark")
-    ap.add_argument("--only", choices=["small", "3f", "batched", "extended", "adjoint", "range"],
+    ap.add_argument("--only", choices=["small", "3f", "batched", "extended", "adjoint", "range", "range3f"],
                     help="with --configs: measure one of the workloads")
     args = ap.parse_args()
     if args.compare_integrators:
